@@ -1,0 +1,229 @@
+/*
+ * epie.h -- C ABI of the GB300 live ePIE engine.
+ *
+ * The engine reconstructs an object O (H x W complex) and an illumination
+ * (probe) P (N x N complex) from far-field diffraction frames with ePIE
+ * (Maiden & Rodenburg 2009), the algorithm the paper runs (Sec. "ePIE
+ * Implementation"), in the paper's live mode: frames are appended to a
+ * growing, device-resident set while sweeps continue (Sec. "Extensions of the
+ * ePIE implementation"; Sec. "Live ePIE": between iterations the processing
+ * thread loads new data and pushes intermediate state to a display).  The
+ * object and probe sizes and the pixel grid are fixed at initialisation from
+ * the nominal scan (Sec. "Determine parameters").
+ *
+ * One ePIE step at scan position j (patch top-left R_j = (y_j, x_j)):
+ *   psi   = P . O_j                     O_j = O[y_j : y_j+N, x_j : x_j+N]
+ *   Psi   = F psi                       unnormalised 2-D DFT, exp(-2 pi i k.r/N)
+ *   Psi'  = sqrt(I_j) Psi/|Psi|         (sqrt(I_j) where |Psi| = 0)
+ *   psi'  = F^-1 Psi'                   includes 1/N^2
+ *   Delta = psi' - psi
+ *   O_j  += alpha conj(P)/max|P|^2 Delta
+ *   P    += beta conj(O_j,old)/max|O_j,old|^2 Delta     (pre-step O_j and P)
+ * A zero maximum turns its update off.  I_j = max(frame_j - dark, 0) (NaN
+ * counts as below 0), with the
+ * frame's zero frequency moved from the detector centre (N/2, N/2) to index 0.
+ * Sweep modes (every sweep visits each frame present at its start once, in a
+ * random order drawn from the handle's seed and the sweep index, as the
+ * paper's engine shuffles per iteration):
+ *   EPIE_SEQUENTIAL  one position at a time (classic ePIE);
+ *   EPIE_COLOURED    positions are grouped into colour classes whose patches
+ *                    do not overlap (greedy first-fit in append order); a
+ *                    class runs in parallel from the probe at class start and
+ *                    the probe moves by the mean of its members' updates;
+ *                    with one member per class this is EPIE_SEQUENTIAL;
+ *   EPIE_MINIBATCH   consecutive batches of `batch` positions share the
+ *                    batch-start O and P; object updates are divided by the
+ *                    per-pixel number of covering patches, probe updates
+ *                    averaged.
+ * The sweep error is E = sum_j sum_k (|Psi_j| - sqrt(I_j))^2 / sum_j sum_k I_j
+ * (the paper defines none), accumulated in FP64.
+ *
+ * Visiting order of sweep s: SplitMix64 stream with state
+ * seed ^ (s * 0xD1B54A32D192ED03); Fisher-Yates (for i = n-1 .. 1,
+ * j = next() mod (i+1)) over the frames (sequential, mini-batch) or over the
+ * class ids and then, with the same stream, over each class's members listed
+ * in append order (coloured).
+ *
+ * Conventions for every call:
+ *   - Complex arrays are interleaved float32 (re, im), row-major.
+ *   - Host buffers belong to the caller; a call has finished reading or
+ *     writing them when it returns.  The engine owns all device memory.
+ *   - Calls on one handle are serialised by a mutex; epie_iterate releases it
+ *     between sweeps, so frames appended by another thread during
+ *     epie_iterate join at the next sweep boundary.
+ *   - Every call returns EPIE_OK (0) or a negative status; epie_error() then
+ *     holds a message.  After EPIE_ECUDA or EPIE_ETIMEOUT the handle only
+ *     accepts epie_error and epie_destroy (EPIE_ESTATE otherwise).
+ *   - There is no CPU fallback: a host without a usable CUDA device gets
+ *     EPIE_ECUDA from epie_init.
+ */
+#ifndef EPIE_H
+#define EPIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EPIE_API __attribute__((visibility("default")))
+#else
+#define EPIE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epie_ctx *epie_t;
+
+/* status codes */
+#define EPIE_OK 0
+#define EPIE_EINVAL (-1)     /* bad argument, size or configuration            */
+#define EPIE_ERANGE (-2)     /* a patch is not fully inside the object          */
+#define EPIE_ECAPACITY (-3)  /* append beyond the capacity fixed at init        */
+#define EPIE_ECUDA (-4)      /* CUDA error (device lost, out of memory, ...)    */
+#define EPIE_ETIMEOUT (-5)   /* a bounded device-side wait expired              */
+#define EPIE_ENUMERIC (-6)   /* the sweep error is not finite                   */
+#define EPIE_ESTATE (-7)     /* handle unusable after a fatal error             */
+
+/* intensity element types (as passed by the caller and as stored on device) */
+#define EPIE_U16 0           /* uint16 counts                                    */
+#define EPIE_F16 1           /* IEEE binary16                                    */
+#define EPIE_F32 2           /* float32                                          */
+
+/* sweep modes */
+#define EPIE_SEQUENTIAL 0
+#define EPIE_COLOURED 1
+#define EPIE_MINIBATCH 2
+
+/* normaliser of the probe update */
+#define EPIE_OMAX_PATCH 0    /* max |O|^2 over the position's patch (default)    */
+#define EPIE_OMAX_GLOBAL 1   /* max |O|^2 over the whole object at group start   */
+
+/* compute path */
+#define EPIE_PATH_FUSED 0    /* one fused kernel per group (default)            */
+#define EPIE_PATH_PLAIN 1    /* separate gather / FFT / modulus / IFFT / update */
+
+/* flags */
+#define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
+                                the sweep error is not finite                   */
+#define EPIE_PROBE_SUM 2u    /* coloured: probe moves by the sum, not the mean  */
+
+typedef struct {
+  int32_t N;               /* frame side: 64, 128, 256 or 512 (2^n frames, Sec.
+                              "ePIE Implementation")                            */
+  int32_t obj_h, obj_w;    /* object size, fixed at init (Sec. "Determine
+                              parameters"); each >= N                           */
+  int32_t capacity;        /* maximum number of frames ever held on device     */
+  int32_t intensity_dtype; /* EPIE_U16 | EPIE_F16 | EPIE_F32                    */
+  int32_t mode;            /* EPIE_SEQUENTIAL | EPIE_COLOURED | EPIE_MINIBATCH  */
+  int32_t batch;           /* EPIE_MINIBATCH: positions per batch (>= 1)        */
+  int32_t omax_mode;       /* EPIE_OMAX_PATCH | EPIE_OMAX_GLOBAL                */
+  int32_t path;            /* EPIE_PATH_FUSED | EPIE_PATH_PLAIN                 */
+  float alpha, beta;       /* update strengths; the paper uses 1 and 1          */
+  uint64_t seed;           /* visiting-order seed                              */
+  int32_t device;          /* CUDA device ordinal                              */
+  void *stream;            /* cudaStream_t to run on, or NULL for an own stream */
+  uint32_t flags;          /* EPIE_CHECKED | EPIE_PROBE_SUM                     */
+} epie_config;
+
+/* Fills *cfg with defaults: N 256, object 1024^2, capacity 1024, EPIE_U16,
+ * EPIE_COLOURED, batch 64, EPIE_OMAX_PATCH, EPIE_PATH_FUSED, alpha = beta = 1,
+ * seed 0, device 0, own stream, no flags. */
+EPIE_API void epie_config_default(epie_config *cfg);
+
+/* Creates a handle and allocates every device buffer the configuration needs.
+ * probe0: N*N complex (required).  object0: obj_h*obj_w complex, or NULL for
+ * an object of ones (the paper's "identity" start, Sec. "Results").
+ * Returns EPIE_EINVAL for a bad configuration, EPIE_ECUDA when the device
+ * cannot be used or memory runs out (*out is then NULL). */
+EPIE_API int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const float *object0);
+
+/* Dark-offset field subtracted from every frame (clamped at 0) before the
+ * modulus replacement.  dark: N*N float32 in the detector (DC-centred) layout
+ * of the frames, or NULL to remove it.  Takes effect at the next sweep. */
+EPIE_API int epie_set_dark(epie_t h, const float *dark);
+
+/* Live ingest (paper, Sec. "Extensions of the ePIE implementation"): appends
+ * n frames and their positions.  frames: n*N*N host values of the handle's
+ * intensity type, DC-centred detector layout; pos_yx: n*(y, x) int32 patch
+ * top-left object pixels.  The frames are copied (through pinned staging
+ * unless `frames` is itself page-locked) and re-laid out on the device;
+ * colour classes are extended.  Fails without side effects with
+ * EPIE_ECAPACITY (would exceed capacity) or EPIE_ERANGE (a patch leaves the
+ * object).  n = 0 is a no-op. */
+EPIE_API int epie_append_frames(epie_t h, const void *frames, const int32_t *pos_yx, int32_t n);
+
+/* As epie_append_frames, with `frames_dev` a device pointer (n*N*N values,
+ * same layout) that must stay valid until the call returns. */
+EPIE_API int epie_append_frames_device(epie_t h, const void *frames_dev, const int32_t *pos_yx,
+                              int32_t n);
+
+/* Drops every frame appended after the first n_keep (to re-attach to a
+ * restarted scan, paper Sec. "Live processing"); colour classes revert to
+ * their state at n_keep frames.  0 <= n_keep <= current count. */
+EPIE_API int epie_truncate_frames(epie_t h, int32_t n_keep);
+
+/* Runs n_sweeps sweeps (n_sweeps >= 0) over the frames present at the start
+ * of each sweep.  err_per_sweep: n_sweeps doubles receiving the sweep error
+ * E, or NULL.  Returns EPIE_ENUMERIC if a sweep error is not finite (with
+ * EPIE_CHECKED, O and P are then back at that sweep's start).  A sweep over
+ * zero frames leaves the state unchanged and reports E = 0. */
+EPIE_API int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep);
+
+/* Object (obj_h*obj_w complex) and probe (N*N complex) export / import at a
+ * sweep boundary (paper, Sec. "Discussion": import and export of object and
+ * illumination through the API).  n_floats must equal 2*obj_h*obj_w or
+ * 2*N*N. */
+EPIE_API int epie_get_object(epie_t h, float *dst, size_t n_floats);
+EPIE_API int epie_get_probe(epie_t h, float *dst, size_t n_floats);
+EPIE_API int epie_set_object(epie_t h, const float *src, size_t n_floats);
+EPIE_API int epie_set_probe(epie_t h, const float *src, size_t n_floats);
+
+/* Number of frames held; number of colour classes. */
+EPIE_API int epie_num_frames(epie_t h, int32_t *n);
+EPIE_API int epie_num_classes(epie_t h, int32_t *n);
+
+/* Colour class of each of the first n frames (n <= frame count). */
+EPIE_API int epie_get_colours(epie_t h, int32_t *colour, int32_t n);
+
+/* Visiting order of sweep `sweep` over the current frames, as the next
+ * epie_iterate would run it: order[count] frame ids and group_start[n_groups+1]
+ * offsets (a group shares the probe at group start).  order must hold the frame
+ * count, group_start the frame count + 1. */
+EPIE_API int epie_get_order(epie_t h, int64_t sweep, int32_t *order, int32_t *group_start,
+                   int32_t *n_groups);
+
+/* Index of the next sweep (starts at 0; used to draw its order).  Setting it
+ * resumes a run that was exported and re-imported. */
+EPIE_API int epie_get_sweep_index(epie_t h, int64_t *sweep);
+EPIE_API int epie_set_sweep_index(epie_t h, int64_t sweep);
+
+/* Device time of the last epie_iterate call in milliseconds (CUDA events on
+ * the handle's stream) and the number of kernels it launched. */
+EPIE_API int epie_last_timing(epie_t h, double *ms, int64_t *kernels);
+
+/* Total number of kernels this handle has launched since epie_init (all
+ * calls: ingest, step, reductions; library calls such as cuFFT excluded). */
+EPIE_API int epie_launch_count(epie_t h, int64_t *total);
+
+/* Step-kernel timing.  While on, epie_iterate brackets every launch of the
+ * position-update step (the fused kernel, or the plain path's gather ... update
+ * sequence) with CUDA events on the handle's stream and resolves them at the
+ * end of each sweep.  epie_kernel_timing returns the totals since the last
+ * call (launches, summed device milliseconds, frames processed) and resets
+ * them. */
+EPIE_API int epie_set_kernel_timing(epie_t h, int32_t on);
+EPIE_API int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t *frames);
+
+/* Message of the handle's last error (or of the last failed epie_init in
+ * this thread when h is NULL).  Valid until the next call on the handle. */
+EPIE_API const char *epie_error(epie_t h);
+
+/* Releases the handle and its device memory.  NULL is a no-op. */
+EPIE_API int epie_destroy(epie_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIE_H */

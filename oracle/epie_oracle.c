@@ -31,7 +31,7 @@
  *   R4 max|O|^2 is taken over the patch O_j by default, or over the whole
  *      object at group start (omax_global).  A zero maximum turns the
  *      corresponding update off (0/0 := 0).
- *   R5 Negative intensities after dark subtraction are clamped to 0.
+ *   R5 Intensities below 0 after dark subtraction, and NaN, are clamped to 0.
  *   R6 Coloured sweep: greedy first-fit colour classes in append order;
  *      members of a class share the probe at class start; the probe moves
  *      by the mean (or sum) of the members' probe updates.

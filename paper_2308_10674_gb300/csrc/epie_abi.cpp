@@ -1,0 +1,872 @@
+// epie_abi.cpp -- host side of the GB300 live ePIE engine: the C ABI of
+// include/epie.h, device memory, the live frame set, colour classes, the
+// per-sweep visiting order and the launch sequence of a sweep.
+//
+// The paper's engine (Sec. "ePIE Implementation") iterates over the
+// diffraction patterns in a randomly shuffled order for a fixed number of
+// iterations; its live extension (Sec. "Extensions of the ePIE
+// implementation", Sec. "Live ePIE") adds patterns between iterations and
+// exports intermediate object and illumination.  Here that control loop is
+// native code around hand-written kernels; PyTorch is not involved.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/epie.h"
+#include "epie_internal.h"
+
+using epie::GroupArgs;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+// ------------------------------------------------------------------ order stream
+// SplitMix64 (Steele, Lea & Flood 2014) with the sweep state of include/epie.h.
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+};
+
+void shuffle(int32_t *a, int32_t n, SplitMix64 &g) {
+  for (int32_t i = n - 1; i >= 1; --i) {
+    const int32_t j = static_cast<int32_t>(g.next() % static_cast<uint64_t>(i + 1));
+    std::swap(a[i], a[j]);
+  }
+}
+
+size_t esize_of(int dtype) { return dtype == EPIE_F32 ? 4 : 2; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct epie_ctx {
+  std::mutex mu;
+  epie_config cfg{};
+  std::string err;
+  bool dead = false;
+  int K = 0;                    // N*N
+  long long HW = 0;             // obj_h*obj_w
+  cudaStream_t st = nullptr;    // compute stream
+  cudaStream_t up = nullptr;    // upload stream (appends)
+  bool own_stream = false;
+  cudaEvent_t ev_up = nullptr;  // last upload finished
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+  double last_ms = 0.0;
+  int64_t last_kernels = 0;
+  int64_t launches_total = 0;
+  // step-kernel timing
+  bool ktime = false;
+  std::vector<cudaEvent_t> kev;   // pairs (start, stop)
+  std::vector<int> kev_frames;
+  int kev_used = 0;
+  int64_t kt_launches = 0, kt_frames = 0;
+  double kt_ms = 0.0;
+
+  // device state
+  float2 *O = nullptr, *P = nullptr, *twiddle = nullptr;
+  void *frames = nullptr;
+  int32_t *pos_d = nullptr, *order_d = nullptr;
+  float *dark_d = nullptr;
+  bool has_dark = false;
+  float2 *probe_part = nullptr;
+  int part_cap = 0;             // members the probe_part buffer holds
+  double *err_part = nullptr, *isum_part = nullptr;
+  int err_stride = 1;
+  unsigned long long *pmax2 = nullptr;  // [2] double bits
+  int pslot = 0;                        // slot holding max|P|^2 of the current probe
+  double *omax_glob = nullptr;
+  unsigned long long *omax_tmp = nullptr;
+  double *err_out = nullptr;            // per-sweep errors of one chunk
+  int *flag_d = nullptr;
+  // checked mode
+  float2 *O_keep = nullptr, *P_keep = nullptr;
+  // plain path
+  float2 *psi = nullptr;
+  int psi_cap = 0;
+  double *omax_m = nullptr;
+  std::map<int, cufftHandle> plans;
+  // mini-batch accumulators
+  float2 *accO = nullptr;
+  int *cnt = nullptr;
+  // staging for appends
+  void *stage_h[2] = {nullptr, nullptr};
+  void *stage_d = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+  int stage_next = 0;
+  double *err_h = nullptr;              // pinned copy of err_out
+
+  // host state
+  int32_t n_frames = 0;
+  std::vector<int32_t> pos_h;           // 2 per frame
+  std::vector<int32_t> colour;          // per frame
+  std::vector<std::vector<int32_t>> classes;  // members in append order
+  std::vector<std::vector<int32_t>> cells;    // frame ids per grid cell
+  int cell_rows = 0, cell_cols = 0;
+  std::vector<uint32_t> stamp;          // per class: last frame that marked it
+  int64_t sweep = 0;
+
+  int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    if (code == EPIE_ECUDA || code == EPIE_ETIMEOUT) dead = true;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char *what) {
+    return fail(EPIE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+};
+
+#define CK(expr)                                     \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return h->cuda_fail(e_, #expr); \
+  } while (0)
+
+namespace {
+
+int check_handle(epie_t h) {
+  if (!h) return EPIE_EINVAL;
+  if (h->dead) return h->fail(EPIE_ESTATE, "handle unusable after an earlier fatal error: %s",
+                               h->err.c_str());
+  return EPIE_OK;
+}
+
+// greedy first-fit colour of a new frame; frames conflict iff their patches
+// overlap (|dy| < N and |dx| < N).  A uniform grid of N x N cells finds the
+// candidates.
+void colour_append(epie_ctx *h, int32_t f) {
+  const int N = h->cfg.N;
+  const int y = h->pos_h[2 * f], x = h->pos_h[2 * f + 1];
+  const int cy = y / N, cx = x / N;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int ry = cy + dy, rx = cx + dx;
+      if (ry < 0 || rx < 0 || ry >= h->cell_rows || rx >= h->cell_cols) continue;
+      for (int32_t g : h->cells[static_cast<size_t>(ry) * h->cell_cols + rx]) {
+        if (std::abs(h->pos_h[2 * g] - y) < N && std::abs(h->pos_h[2 * g + 1] - x) < N)
+          h->stamp[h->colour[g]] = static_cast<uint32_t>(f) + 1u;
+      }
+    }
+  int32_t c = 0;
+  const int32_t nc = static_cast<int32_t>(h->classes.size());
+  while (c < nc && h->stamp[c] == static_cast<uint32_t>(f) + 1u) ++c;
+  if (c == nc) {
+    h->classes.emplace_back();
+    h->stamp.push_back(0);
+  }
+  h->colour[f] = c;
+  h->classes[c].push_back(f);
+  h->cells[static_cast<size_t>(cy) * h->cell_cols + cx].push_back(f);
+}
+
+// visiting order of sweep s over the first n frames (include/epie.h)
+void make_order(const epie_ctx *h, int64_t s, int32_t n, std::vector<int32_t> &order,
+                std::vector<int32_t> &gstart) {
+  SplitMix64 g{h->cfg.seed ^ (static_cast<uint64_t>(s) * 0xD1B54A32D192ED03ULL)};
+  order.resize(n);
+  gstart.clear();
+  if (h->cfg.mode == EPIE_COLOURED) {
+    const int32_t nc = static_cast<int32_t>(h->classes.size());
+    std::vector<int32_t> cls(nc);
+    for (int32_t c = 0; c < nc; ++c) cls[c] = c;
+    shuffle(cls.data(), nc, g);
+    int32_t p = 0;
+    for (int32_t c : cls) {
+      gstart.push_back(p);
+      const int32_t a = p;
+      for (int32_t f : h->classes[c])
+        if (f < n) order[p++] = f;
+      shuffle(order.data() + a, p - a, g);
+    }
+    gstart.push_back(p);
+  } else {
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    shuffle(order.data(), n, g);
+    const int32_t B = h->cfg.mode == EPIE_MINIBATCH ? h->cfg.batch : 1;
+    for (int32_t a = 0; a < n; a += B) gstart.push_back(a);
+    gstart.push_back(n);
+  }
+}
+
+int ensure_part(epie_ctx *h, int members) {
+  if (members <= h->part_cap) return EPIE_OK;
+  int cap = std::max(members, h->part_cap * 2);
+  if (h->probe_part) cudaFree(h->probe_part);
+  h->probe_part = nullptr;
+  h->part_cap = 0;
+  CK(cudaMalloc(&h->probe_part, sizeof(float2) * static_cast<size_t>(cap) * h->K));
+  h->part_cap = cap;
+  if (h->cfg.path == EPIE_PATH_PLAIN) {
+    if (h->psi) cudaFree(h->psi);
+    if (h->omax_m) cudaFree(h->omax_m);
+    h->psi = nullptr;
+    h->omax_m = nullptr;
+    CK(cudaMalloc(&h->psi, sizeof(float2) * static_cast<size_t>(cap) * h->K));
+    CK(cudaMalloc(&h->omax_m, sizeof(double) * cap));
+    h->psi_cap = cap;
+  }
+  return EPIE_OK;
+}
+
+int get_plan(epie_ctx *h, int batch, cufftHandle *out) {
+  auto it = h->plans.find(batch);
+  if (it != h->plans.end()) {
+    *out = it->second;
+    return EPIE_OK;
+  }
+  cufftHandle p;
+  int n[2] = {h->cfg.N, h->cfg.N};
+  if (cufftPlanMany(&p, 2, n, nullptr, 1, h->K, nullptr, 1, h->K, CUFFT_C2C, batch) != CUFFT_SUCCESS)
+    return h->fail(EPIE_ECUDA, "cufftPlanMany(batch %d) failed", batch);
+  if (cufftSetStream(p, h->st) != CUFFT_SUCCESS) return h->fail(EPIE_ECUDA, "cufftSetStream failed");
+  h->plans[batch] = p;
+  *out = p;
+  return EPIE_OK;
+}
+
+// One group: fused kernel (or the plain sequence), then the probe reduction.
+int run_group(epie_ctx *h, const int32_t *members_d, int n_members, int64_t *kernels) {
+  const int N = h->cfg.N;
+  int rc = ensure_part(h, n_members);
+  if (rc) return rc;
+  const bool mb = h->cfg.mode == EPIE_MINIBATCH;
+  GroupArgs a{};
+  a.O = h->O;
+  a.W = h->cfg.obj_w;
+  a.P = h->P;
+  a.frames = h->frames;
+  a.dark = h->has_dark ? h->dark_d : nullptr;
+  a.pos = h->pos_d;
+  a.members = members_d;
+  a.n_members = n_members;
+  a.probe_part = h->probe_part;
+  a.err_part = h->err_part;
+  a.isum_part = h->isum_part;
+  a.err_stride = h->err_stride;
+  a.pmax2 = h->pmax2 + h->pslot;
+  a.pmax2_clear = h->pmax2 + (h->pslot ^ 1);
+  a.twiddle = h->twiddle;
+  a.alpha = h->cfg.alpha;
+  a.beta = h->cfg.beta;
+  a.err_flag = h->flag_d;
+  a.accO = mb ? h->accO : nullptr;
+  a.cnt = mb ? h->cnt : nullptr;
+  if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
+    CK(epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st));
+    a.omax2_global = h->omax_glob;
+    *kernels += 2;
+  }
+  if (h->ktime) {
+    if (h->kev_used + 2 > static_cast<int>(h->kev.size())) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->kev.push_back(e);
+      }
+      h->kev_frames.resize(h->kev.size() / 2);
+    }
+    h->kev_frames[h->kev_used / 2] = n_members;
+    CK(cudaEventRecord(h->kev[h->kev_used], h->st));
+  }
+  if (h->cfg.path == EPIE_PATH_FUSED) {
+    CK(epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st));
+    *kernels += 1;
+  } else {
+    cufftHandle plan;
+    if ((rc = get_plan(h, n_members, &plan))) return rc;
+    CK(epie::launch_plain_gather(a, N, h->psi, h->omax_m, h->st));
+    auto *z = reinterpret_cast<cufftComplex *>(h->psi);
+    if (cufftExecC2C(plan, z, z, CUFFT_FORWARD) != CUFFT_SUCCESS)
+      return h->fail(EPIE_ECUDA, "cufftExecC2C forward failed");
+    CK(epie::launch_plain_modulus(a, N, h->cfg.intensity_dtype, h->psi, h->st));
+    if (cufftExecC2C(plan, z, z, CUFFT_INVERSE) != CUFFT_SUCCESS)
+      return h->fail(EPIE_ECUDA, "cufftExecC2C inverse failed");
+    if (mb)
+      CK(epie::launch_mb_accumulate(a, N, h->psi, h->omax_m, h->accO, h->cnt, h->st));
+    else
+      CK(epie::launch_plain_update(a, N, h->psi, h->omax_m, h->st));
+    *kernels += 3;  // gather, modulus, update (the two transforms are cuFFT's)
+  }
+  if (h->ktime) {
+    CK(cudaEventRecord(h->kev[h->kev_used + 1], h->st));
+    h->kev_used += 2;
+  }
+  if (mb) {
+    CK(epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st));
+    *kernels += 1;
+  }
+  const bool mean = h->cfg.mode == EPIE_MINIBATCH ||
+                    (h->cfg.mode == EPIE_COLOURED && !(h->cfg.flags & EPIE_PROBE_SUM));
+  const float scale = mean ? 1.0f / static_cast<float>(n_members) : 1.0f;
+  CK(epie::launch_probe_reduce(h->P, h->probe_part, n_members, N, scale,
+                               h->pmax2 + (h->pslot ^ 1), h->st));
+  *kernels += 1;
+  h->pslot ^= 1;
+  return EPIE_OK;
+}
+
+int recompute_pmax(epie_ctx *h) {
+  CK(cudaMemsetAsync(h->pmax2 + h->pslot, 0, sizeof(unsigned long long), h->st));
+  CK(epie::launch_probe_max(h->P, h->K, h->pmax2 + h->pslot, h->st));
+  h->launches_total += 1;
+  return EPIE_OK;
+}
+
+// one sweep over the frames present now; writes the sweep error to err_out[slot]
+int run_sweep(epie_ctx *h, int slot, int64_t *kernels) {
+  const int32_t n = h->n_frames;
+  CK(cudaStreamWaitEvent(h->st, h->ev_up, 0));
+  if (h->cfg.flags & EPIE_CHECKED) {
+    CK(cudaMemcpyAsync(h->O_keep, h->O, sizeof(float2) * h->HW, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->P_keep, h->P, sizeof(float2) * h->K, cudaMemcpyDeviceToDevice, h->st));
+  }
+  if (n == 0) {
+    CK(cudaMemsetAsync(h->err_out + slot, 0, sizeof(double), h->st));
+    return EPIE_OK;
+  }
+  std::vector<int32_t> order, gstart;
+  make_order(h, h->sweep, n, order, gstart);
+  CK(cudaMemcpyAsync(h->order_d, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st));
+  const int ng = static_cast<int>(gstart.size()) - 1;
+  for (int g = 0; g < ng; ++g) {
+    const int m = gstart[g + 1] - gstart[g];
+    if (m == 0) continue;
+    int rc = run_group(h, h->order_d + gstart[g], m, kernels);
+    if (rc) return rc;
+  }
+  CK(epie::launch_error_reduce(h->err_part, h->isum_part, n, h->err_stride, h->err_out + slot,
+                               h->st));
+  *kernels += 1;
+  if (h->ktime && h->kev_used > 0) {
+    CK(cudaEventSynchronize(h->kev[h->kev_used - 1]));
+    for (int i = 0; i < h->kev_used; i += 2) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->kev[i], h->kev[i + 1]));
+      h->kt_ms += ms;
+      h->kt_launches += 1;
+      h->kt_frames += h->kev_frames[i / 2];
+    }
+    h->kev_used = 0;
+  }
+  return EPIE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+void epie_config_default(epie_config *c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->N = 256;
+  c->obj_h = c->obj_w = 1024;
+  c->capacity = 1024;
+  c->intensity_dtype = EPIE_U16;
+  c->mode = EPIE_COLOURED;
+  c->batch = 64;
+  c->omax_mode = EPIE_OMAX_PATCH;
+  c->path = EPIE_PATH_FUSED;
+  c->alpha = c->beta = 1.0f;
+  c->seed = 0;
+  c->device = 0;
+  c->stream = nullptr;
+  c->flags = 0;
+}
+
+const char *epie_error(epie_t h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+int epie_destroy(epie_t h) {
+  if (!h) return EPIE_OK;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaSetDevice(h->cfg.device);
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->up) cudaStreamSynchronize(h->up);
+    for (auto &kv : h->plans) cufftDestroy(kv.second);
+    void *dev[] = {h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
+                   h->probe_part, h->err_part, h->isum_part, h->pmax2, h->omax_glob,
+                   h->omax_tmp, h->err_out, h->flag_d, h->O_keep, h->P_keep, h->psi,
+                   h->omax_m, h->accO, h->cnt, h->stage_d};
+    for (void *p : dev)
+      if (p) cudaFree(p);
+    for (void *p : h->stage_h)
+      if (p) cudaFreeHost(p);
+    if (h->err_h) cudaFreeHost(h->err_h);
+    for (cudaEvent_t e : {h->ev_up, h->ev_t0, h->ev_t1, h->ev_stage[0], h->ev_stage[1]})
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->kev) cudaEventDestroy(e);
+    if (h->up) cudaStreamDestroy(h->up);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  }
+  delete h;
+  return EPIE_OK;
+}
+
+static int init_fail(epie_t h, int code) {
+  g_init_error = h->err;
+  epie_destroy(h);
+  return code;
+}
+
+int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const float *object0) {
+  if (!out) {
+    g_init_error = "epie_init: out is NULL";
+    return EPIE_EINVAL;
+  }
+  *out = nullptr;
+  if (!cfg || !probe0) {
+    g_init_error = "epie_init: cfg and probe0 are required";
+    return EPIE_EINVAL;
+  }
+  const epie_config c = *cfg;
+  std::string why;
+  if (!(c.N == 64 || c.N == 128 || c.N == 256 || c.N == 512)) why = "N must be 64, 128, 256 or 512";
+  else if (c.obj_h < c.N || c.obj_w < c.N) why = "object must be at least N x N";
+  else if (static_cast<long long>(c.obj_h) * c.obj_w > (1LL << 31)) why = "object too large";
+  else if (c.capacity < 0) why = "capacity must be >= 0";
+  else if (c.intensity_dtype < EPIE_U16 || c.intensity_dtype > EPIE_F32) why = "bad intensity_dtype";
+  else if (c.mode < EPIE_SEQUENTIAL || c.mode > EPIE_MINIBATCH) why = "bad mode";
+  else if (c.mode == EPIE_MINIBATCH && c.batch < 1) why = "batch must be >= 1";
+  else if (c.omax_mode != EPIE_OMAX_PATCH && c.omax_mode != EPIE_OMAX_GLOBAL) why = "bad omax_mode";
+  else if (c.path != EPIE_PATH_FUSED && c.path != EPIE_PATH_PLAIN) why = "bad path";
+  else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
+  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM)) why = "unknown flags";
+  if (!why.empty()) {
+    g_init_error = "epie_init: " + why;
+    return EPIE_EINVAL;
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) {
+    g_init_error = std::string("epie_init: no CUDA device: ") + cudaGetErrorString(ce);
+    return EPIE_ECUDA;
+  }
+  if (c.device < 0 || c.device >= ndev) {
+    g_init_error = "epie_init: device ordinal out of range";
+    return EPIE_EINVAL;
+  }
+  epie_t h = new epie_ctx;
+  h->cfg = c;
+  h->K = c.N * c.N;
+  h->HW = static_cast<long long>(c.obj_h) * c.obj_w;
+  // partial error slots per frame: one per CTA of the fused kernel, one per
+  // block of the plain path's modulus kernel; every slot is written each sweep
+  h->err_stride = c.path == EPIE_PATH_FUSED ? epie::fused_ctas_per_frame(c.N)
+                                            : epie::plain_err_stride(c.N);
+  h->cell_rows = (c.obj_h + c.N - 1) / c.N;
+  h->cell_cols = (c.obj_w + c.N - 1) / c.N;
+  h->cells.resize(static_cast<size_t>(h->cell_rows) * h->cell_cols);
+  const int cap = std::max(c.capacity, 1);
+  const size_t es = esize_of(c.intensity_dtype);
+#define IK(expr)                                      \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) {                          \
+      h->cuda_fail(e_, #expr);                        \
+      return init_fail(h, EPIE_ECUDA);                \
+    }                                                 \
+  } while (0)
+  IK(cudaSetDevice(c.device));
+  if (c.stream) {
+    h->st = static_cast<cudaStream_t>(c.stream);
+  } else {
+    IK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  IK(cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking));
+  IK(cudaEventCreateWithFlags(&h->ev_up, cudaEventDisableTiming));
+  IK(cudaEventCreate(&h->ev_t0));
+  IK(cudaEventCreate(&h->ev_t1));
+  IK(cudaEventCreateWithFlags(&h->ev_stage[0], cudaEventDisableTiming));
+  IK(cudaEventCreateWithFlags(&h->ev_stage[1], cudaEventDisableTiming));
+  IK(cudaEventRecord(h->ev_up, h->up));
+  IK(cudaMalloc(&h->O, sizeof(float2) * h->HW));
+  IK(cudaMalloc(&h->P, sizeof(float2) * h->K));
+  IK(cudaMalloc(&h->twiddle, sizeof(float2) * c.N));
+  IK(cudaMalloc(&h->frames, es * h->K * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->pos_d, sizeof(int32_t) * 2 * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->order_d, sizeof(int32_t) * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->dark_d, sizeof(float) * h->K));
+  IK(cudaMalloc(&h->err_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->isum_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->pmax2, sizeof(unsigned long long) * 2));
+  IK(cudaMalloc(&h->omax_glob, sizeof(double)));
+  IK(cudaMalloc(&h->omax_tmp, sizeof(unsigned long long)));
+  IK(cudaMalloc(&h->err_out, sizeof(double) * 1024));
+  IK(cudaMallocHost(&h->err_h, sizeof(double) * 1024));
+  IK(cudaMalloc(&h->flag_d, sizeof(int)));
+  IK(cudaMemsetAsync(h->flag_d, 0, sizeof(int), h->st));
+  IK(cudaMemsetAsync(h->pmax2, 0, sizeof(unsigned long long) * 2, h->st));
+  if (c.flags & EPIE_CHECKED) {
+    IK(cudaMalloc(&h->O_keep, sizeof(float2) * h->HW));
+    IK(cudaMalloc(&h->P_keep, sizeof(float2) * h->K));
+  }
+  if (c.mode == EPIE_MINIBATCH) {
+    IK(cudaMalloc(&h->accO, sizeof(float2) * h->HW));
+    IK(cudaMalloc(&h->cnt, sizeof(int) * h->HW));
+    IK(cudaMemsetAsync(h->accO, 0, sizeof(float2) * h->HW, h->st));
+    IK(cudaMemsetAsync(h->cnt, 0, sizeof(int) * h->HW, h->st));
+  }
+  {
+    const int pre = c.mode == EPIE_MINIBATCH ? c.batch : (c.mode == EPIE_SEQUENTIAL ? 1 : 64);
+    if (ensure_part(h, pre) != EPIE_OK) return init_fail(h, EPIE_ECUDA);
+  }
+  // staging: two pinned host buffers and one device buffer of whole frames
+  {
+    const size_t frame_bytes = es * h->K;
+    const size_t want = std::max<size_t>(frame_bytes, (size_t)64 << 20);
+    h->stage_bytes = want / frame_bytes * frame_bytes;
+    IK(cudaMallocHost(&h->stage_h[0], h->stage_bytes));
+    IK(cudaMallocHost(&h->stage_h[1], h->stage_bytes));
+    IK(cudaMalloc(&h->stage_d, h->stage_bytes));
+    IK(cudaEventRecord(h->ev_stage[0], h->up));
+    IK(cudaEventRecord(h->ev_stage[1], h->up));
+  }
+  // twiddles exp(-2 pi i m / N), evaluated in double precision on the host
+  {
+    std::vector<float2> tw(c.N);
+    for (int m = 0; m < c.N; ++m) {
+      const double ang = -2.0 * 3.14159265358979323846 * m / c.N;
+      tw[m] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
+    }
+    IK(cudaMemcpy(h->twiddle, tw.data(), sizeof(float2) * c.N, cudaMemcpyHostToDevice));
+  }
+  IK(cudaMemcpy(h->P, probe0, sizeof(float2) * h->K, cudaMemcpyHostToDevice));
+  if (object0) {
+    IK(cudaMemcpy(h->O, object0, sizeof(float2) * h->HW, cudaMemcpyHostToDevice));
+  } else {
+    IK(epie::launch_fill(h->O, h->HW, make_float2(1.f, 0.f), h->st));
+  }
+  if (recompute_pmax(h) != EPIE_OK) return init_fail(h, EPIE_ECUDA);
+  IK(cudaStreamSynchronize(h->st));
+#undef IK
+  *out = h;
+  return EPIE_OK;
+}
+
+int epie_set_dark(epie_t h, const float *dark) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  CK(cudaSetDevice(h->cfg.device));
+  if (!dark) {
+    h->has_dark = false;
+    return EPIE_OK;
+  }
+  float *tmp = reinterpret_cast<float *>(h->stage_d);
+  CK(cudaStreamWaitEvent(h->st, h->ev_up, 0));
+  CK(cudaMemcpyAsync(tmp, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
+  CK(epie::launch_dark_ingest(tmp, h->dark_d, h->cfg.N, h->st));
+  h->launches_total += 1;
+  CK(cudaStreamSynchronize(h->st));
+  h->has_dark = true;
+  return EPIE_OK;
+}
+
+static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t n, bool device) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (n < 0 || (n > 0 && (!frames || !pos))) return h->fail(EPIE_EINVAL, "append: bad arguments");
+  if (n == 0) return EPIE_OK;
+  const int N = h->cfg.N;
+  if (static_cast<long long>(h->n_frames) + n > h->cfg.capacity)
+    return h->fail(EPIE_ECAPACITY, "append: %d + %d frames exceed capacity %d", h->n_frames, n,
+                   h->cfg.capacity);
+  for (int32_t i = 0; i < n; ++i) {
+    const int y = pos[2 * i], x = pos[2 * i + 1];
+    if (y < 0 || x < 0 || y > h->cfg.obj_h - N || x > h->cfg.obj_w - N)
+      return h->fail(EPIE_ERANGE, "append: frame %d at (%d, %d) leaves the %d x %d object", i, y,
+                     x, h->cfg.obj_h, h->cfg.obj_w);
+  }
+  CK(cudaSetDevice(h->cfg.device));
+  const size_t es = esize_of(h->cfg.intensity_dtype);
+  const size_t fb = es * h->K;
+  const int per = static_cast<int>(h->stage_bytes / fb);
+  char *dst0 = static_cast<char *>(h->frames) + fb * static_cast<size_t>(h->n_frames);
+  bool pinned = false;
+  if (!device) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, frames) == cudaSuccess && at.type == cudaMemoryTypeHost)
+      pinned = true;
+    else
+      cudaGetLastError();
+  }
+  for (int32_t a = 0; a < n; a += per) {
+    const int m = std::min(per, n - a);
+    const char *src = static_cast<const char *>(frames) + fb * static_cast<size_t>(a);
+    if (device || pinned) {
+      // device or page-locked source: one copy into the device staging buffer
+      CK(cudaMemcpyAsync(h->stage_d, src, fb * m,
+                         device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->up));
+    } else {
+      const int b = h->stage_next;
+      h->stage_next ^= 1;
+      CK(cudaEventSynchronize(h->ev_stage[b]));  // buffer b free again
+      std::memcpy(h->stage_h[b], src, fb * m);
+      CK(cudaMemcpyAsync(h->stage_d, h->stage_h[b], fb * m, cudaMemcpyHostToDevice, h->up));
+      CK(cudaEventRecord(h->ev_stage[b], h->up));
+    }
+    CK(epie::launch_ingest(h->stage_d, dst0 + fb * static_cast<size_t>(a), m, N,
+                           static_cast<int>(es), h->up));
+    h->launches_total += 1;
+  }
+  CK(cudaMemcpyAsync(h->pos_d + 2 * static_cast<size_t>(h->n_frames), pos,
+                     sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, h->up));
+  CK(cudaEventRecord(h->ev_up, h->up));
+  // the caller's buffer must be free when we return
+  CK(cudaStreamSynchronize(h->up));
+  const int32_t f0 = h->n_frames;
+  h->pos_h.insert(h->pos_h.end(), pos, pos + 2 * static_cast<size_t>(n));
+  h->colour.resize(static_cast<size_t>(f0) + n);
+  for (int32_t i = 0; i < n; ++i) colour_append(h, f0 + i);
+  h->n_frames = f0 + n;
+  return EPIE_OK;
+}
+
+int epie_append_frames(epie_t h, const void *frames, const int32_t *pos_yx, int32_t n) {
+  return append_impl(h, frames, pos_yx, n, false);
+}
+
+int epie_append_frames_device(epie_t h, const void *frames_dev, const int32_t *pos_yx, int32_t n) {
+  return append_impl(h, frames_dev, pos_yx, n, true);
+}
+
+int epie_truncate_frames(epie_t h, int32_t n_keep) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (n_keep < 0 || n_keep > h->n_frames)
+    return h->fail(EPIE_EINVAL, "truncate: n_keep %d outside [0, %d]", n_keep, h->n_frames);
+  const int N = h->cfg.N;
+  for (int32_t f = h->n_frames - 1; f >= n_keep; --f) {
+    // the newest frame is last in its class and in its grid cell
+    h->classes[h->colour[f]].pop_back();
+    const int cy = h->pos_h[2 * f] / N, cx = h->pos_h[2 * f + 1] / N;
+    h->cells[static_cast<size_t>(cy) * h->cell_cols + cx].pop_back();
+  }
+  while (!h->classes.empty() && h->classes.back().empty()) {
+    h->classes.pop_back();
+    h->stamp.pop_back();
+  }
+  h->pos_h.resize(2 * static_cast<size_t>(n_keep));
+  h->colour.resize(n_keep);
+  h->n_frames = n_keep;
+  return EPIE_OK;
+}
+
+int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (n_sweeps < 0) return h->fail(EPIE_EINVAL, "iterate: n_sweeps < 0");
+  int64_t kernels = 0;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    CK(cudaSetDevice(h->cfg.device));
+    CK(cudaEventRecord(h->ev_t0, h->st));
+  }
+  for (int32_t s = 0; s < n_sweeps; ++s) {
+    std::lock_guard<std::mutex> lk(h->mu);  // appends may slip in between sweeps
+    if (h->dead) return h->fail(EPIE_ESTATE, "handle unusable: %s", h->err.c_str());
+    const int slot = s % 1024;
+    rc = run_sweep(h, slot, &kernels);
+    if (rc) return rc;
+    h->sweep += 1;
+    const bool last = s + 1 == n_sweeps;
+    if (last || slot == 1023 || (h->cfg.flags & EPIE_CHECKED)) {
+      // fetch the errors of this chunk of sweeps and the device status word
+      // slots [first, slot] hold sweeps s - (slot - first) .. s of this call
+      const int first = (h->cfg.flags & EPIE_CHECKED) ? slot : 0;
+      const int cnt = slot - first + 1;
+      CK(cudaMemcpyAsync(h->err_h + first, h->err_out + first, sizeof(double) * cnt,
+                         cudaMemcpyDeviceToHost, h->st));
+      int flag = 0;
+      CK(cudaStreamSynchronize(h->st));
+      CK(cudaMemcpy(&flag, h->flag_d, sizeof(int), cudaMemcpyDeviceToHost));
+      if (flag) return h->fail(EPIE_ETIMEOUT, "a bounded device wait expired (flag %d)", flag);
+      for (int i = first; i <= slot; ++i) {
+        const int32_t sw = s - (slot - i);
+        const double e = h->err_h[i];
+        if (err_per_sweep) err_per_sweep[sw] = e;
+        if (!std::isfinite(e)) {
+          if (h->cfg.flags & EPIE_CHECKED) {
+            CK(cudaMemcpyAsync(h->O, h->O_keep, sizeof(float2) * h->HW, cudaMemcpyDeviceToDevice,
+                               h->st));
+            CK(cudaMemcpyAsync(h->P, h->P_keep, sizeof(float2) * h->K, cudaMemcpyDeviceToDevice,
+                               h->st));
+            if ((rc = recompute_pmax(h))) return rc;
+            CK(cudaStreamSynchronize(h->st));
+            h->sweep -= 1;
+          }
+          return h->fail(EPIE_ENUMERIC, "sweep %lld: error metric is not finite",
+                         static_cast<long long>(h->sweep));
+        }
+      }
+    }
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  CK(cudaEventRecord(h->ev_t1, h->st));
+  CK(cudaEventSynchronize(h->ev_t1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+  h->last_ms = ms;
+  h->last_kernels = kernels;
+  h->launches_total += kernels;
+  return EPIE_OK;
+}
+
+static int copy_state(epie_t h, void *host, const void *dev, size_t bytes, size_t want_floats,
+                      size_t n_floats, bool to_dev, const char *what) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!host || n_floats != want_floats)
+    return h->fail(EPIE_EINVAL, "%s: need %zu floats, got %zu", what, want_floats, n_floats);
+  CK(cudaSetDevice(h->cfg.device));
+  CK(cudaStreamSynchronize(h->st));
+  if (to_dev) {
+    CK(cudaMemcpy(const_cast<void *>(dev), host, bytes, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(host, dev, bytes, cudaMemcpyDeviceToHost));
+  }
+  return EPIE_OK;
+}
+
+int epie_get_object(epie_t h, float *dst, size_t n_floats) {
+  if (!h) return EPIE_EINVAL;
+  return copy_state(h, dst, h->O, sizeof(float2) * h->HW, 2 * static_cast<size_t>(h->HW), n_floats,
+                    false, "get_object");
+}
+
+int epie_get_probe(epie_t h, float *dst, size_t n_floats) {
+  if (!h) return EPIE_EINVAL;
+  return copy_state(h, dst, h->P, sizeof(float2) * h->K, 2 * static_cast<size_t>(h->K), n_floats,
+                    false, "get_probe");
+}
+
+int epie_set_object(epie_t h, const float *src, size_t n_floats) {
+  if (!h) return EPIE_EINVAL;
+  return copy_state(h, const_cast<float *>(src), h->O, sizeof(float2) * h->HW,
+                    2 * static_cast<size_t>(h->HW), n_floats, true, "set_object");
+}
+
+int epie_set_probe(epie_t h, const float *src, size_t n_floats) {
+  if (!h) return EPIE_EINVAL;
+  int rc = copy_state(h, const_cast<float *>(src), h->P, sizeof(float2) * h->K,
+                      2 * static_cast<size_t>(h->K), n_floats, true, "set_probe");
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = recompute_pmax(h))) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  return EPIE_OK;
+}
+
+int epie_num_frames(epie_t h, int32_t *n) {
+  if (!h || !n) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *n = h->n_frames;
+  return EPIE_OK;
+}
+
+int epie_num_classes(epie_t h, int32_t *n) {
+  if (!h || !n) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *n = static_cast<int32_t>(h->classes.size());
+  return EPIE_OK;
+}
+
+int epie_get_colours(epie_t h, int32_t *colour, int32_t n) {
+  if (!h || (!colour && n > 0)) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (n < 0 || n > h->n_frames) return h->fail(EPIE_EINVAL, "get_colours: bad count %d", n);
+  std::copy(h->colour.begin(), h->colour.begin() + n, colour);
+  return EPIE_OK;
+}
+
+int epie_get_order(epie_t h, int64_t sweep, int32_t *order, int32_t *group_start,
+                   int32_t *n_groups) {
+  if (!h || !n_groups) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (h->n_frames > 0 && (!order || !group_start))
+    return h->fail(EPIE_EINVAL, "get_order: NULL output");
+  std::vector<int32_t> o, g;
+  make_order(h, sweep, h->n_frames, o, g);
+  std::copy(o.begin(), o.end(), order);
+  std::copy(g.begin(), g.end(), group_start);
+  *n_groups = static_cast<int32_t>(g.size()) - 1;
+  return EPIE_OK;
+}
+
+int epie_get_sweep_index(epie_t h, int64_t *sweep) {
+  if (!h || !sweep) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *sweep = h->sweep;
+  return EPIE_OK;
+}
+
+int epie_set_sweep_index(epie_t h, int64_t sweep) {
+  if (!h || sweep < 0) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->sweep = sweep;
+  return EPIE_OK;
+}
+
+int epie_last_timing(epie_t h, double *ms, int64_t *kernels) {
+  if (!h) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (ms) *ms = h->last_ms;
+  if (kernels) *kernels = h->last_kernels;
+  return EPIE_OK;
+}
+
+int epie_launch_count(epie_t h, int64_t *total) {
+  if (!h || !total) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *total = h->launches_total;
+  return EPIE_OK;
+}
+
+int epie_set_kernel_timing(epie_t h, int32_t on) {
+  if (!h) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->ktime = on != 0;
+  h->kev_used = 0;
+  return EPIE_OK;
+}
+
+int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t *frames) {
+  if (!h) return EPIE_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (launches) *launches = h->kt_launches;
+  if (ms) *ms = h->kt_ms;
+  if (frames) *frames = h->kt_frames;
+  h->kt_launches = h->kt_frames = 0;
+  h->kt_ms = 0.0;
+  return EPIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,383 @@
+// epie_aux.cu -- kernels around the fused ePIE step: live ingest (DC shift),
+// the per-group probe reduction with its FP64 max|P|^2, FP64 maxima and the
+// sweep-error reduction, and the pieces of the plain unfused path
+// (gather / modulus / update) that runs the same step with cuFFT in between.
+#include <cuda_fp16.h>
+
+#include "epie_fft.cuh"
+#include "epie_internal.h"
+
+namespace epie {
+
+namespace {
+
+// bits of a non-negative double order like the double itself
+__device__ __forceinline__ void atomic_max_pos_double(unsigned long long *slot, double v) {
+  atomicMax(slot, static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// block-wide max of a double (all threads return the block value)
+template <int NT>
+__device__ double block_max(double v, double *sh) {
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = sh[0];
+  for (int w = 1; w < NT / 32; ++w) m = fmax(m, sh[w]);
+  __syncthreads();
+  return m;
+}
+
+// ---------------------------------------------------------------- ingest
+
+// DC-centred detector frame -> FFT order: dst[ky][kx] = src[(ky+N/2)%N][(kx+N/2)%N].
+// Rows hold N*esize bytes (a multiple of 16); the half-row rotation moves
+// whole 16-byte chunks, so each thread copies one uint4.
+__global__ void ingest_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst, int n,
+                              int N, int chunks_per_row) {
+  const long long total = static_cast<long long>(n) * N * chunks_per_row;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(t % chunks_per_row);
+    const long long rowid = t / chunks_per_row;
+    const int ky = static_cast<int>(rowid % N);
+    const long long f = rowid / N;
+    const int sy = (ky + N / 2) % N;
+    const int sc = (c + chunks_per_row / 2) % chunks_per_row;
+    dst[t] = src[(f * N + sy) * chunks_per_row + sc];
+  }
+}
+
+__global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restrict__ dst, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N) return;
+  const int ky = t / N, kx = t % N;
+  dst[t] = src[((ky + N / 2) % N) * N + (kx + N / 2) % N];
+}
+
+// ---------------------------------------------------------------- probe
+
+// P += scale * sum_{m < n_members} part[m] (members in order), then the
+// FP64 max|P|^2 of the new probe (FP32 comparison picks the element).
+template <int NT>
+__global__ void __launch_bounds__(NT) probe_reduce_kernel(float2 *__restrict__ P,
+                                                          const float2 *__restrict__ part,
+                                                          int n_members, int K, float scale,
+                                                          unsigned long long *pmax2_next) {
+  __shared__ double sh[NT / 32];
+  float best = -1.f;
+  float2 bv = make_float2(0.f, 0.f);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < K; i += gridDim.x * NT) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int m = 0; m < n_members; ++m) acc = cadd(acc, part[static_cast<size_t>(m) * K + i]);
+    float2 p = P[i];
+    p.x = fmaf(scale, acc.x, p.x);
+    p.y = fmaf(scale, acc.y, p.y);
+    P[i] = p;
+    const float q = p.x * p.x + p.y * p.y;
+    if (q > best) { best = q; bv = p; }
+  }
+  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
+  d = block_max<NT>(d, sh);
+  if (threadIdx.x == 0) atomic_max_pos_double(pmax2_next, d);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) abs2_max_kernel(const float2 *__restrict__ a, long long n,
+                                                      unsigned long long *out) {
+  __shared__ double sh[NT / 32];
+  float best = -1.f;
+  float2 bv = make_float2(0.f, 0.f);
+  for (long long i = blockIdx.x * static_cast<long long>(NT) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * NT) {
+    const float2 p = a[i];
+    const float q = p.x * p.x + p.y * p.y;
+    if (q > best) { best = q; bv = p; }
+  }
+  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
+  d = block_max<NT>(d, sh);
+  if (threadIdx.x == 0) atomic_max_pos_double(out, d);
+}
+
+__global__ void bits_to_double_kernel(const unsigned long long *bits, double *out) {
+  *out = __longlong_as_double(static_cast<long long>(*bits));
+}
+
+// ---------------------------------------------------------------- sweep error
+
+// One block: thread t sums frames t, t+NT, ... (slots in order), then a
+// fixed tree over threads.  E = sum e / sum s (0 when sum s = 0).
+template <int NT>
+__global__ void __launch_bounds__(NT) error_reduce_kernel(const double *__restrict__ e,
+                                                          const double *__restrict__ s,
+                                                          int n_frames, int stride,
+                                                          double *out) {
+  __shared__ double se[NT], ss[NT];
+  double a = 0.0, b = 0.0;
+  for (int f = threadIdx.x; f < n_frames; f += NT)
+    for (int c = 0; c < stride; ++c) {
+      a += e[static_cast<size_t>(f) * stride + c];
+      b += s[static_cast<size_t>(f) * stride + c];
+    }
+  se[threadIdx.x] = a;
+  ss[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = ss[0] > 0.0 ? se[0] / ss[0] : 0.0;
+}
+
+// ---------------------------------------------------------------- plain path
+
+// psi[m] = P . O_j for every member; max|O_j|^2 per member (bits)
+__global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi,
+                                    unsigned long long *__restrict__ omax_bits) {
+  __shared__ double sh[8];
+  const int m = blockIdx.y, K = N * N;
+  const int f = a.members[m];
+  const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
+  float best = -1.f;
+  float2 bv = make_float2(0.f, 0.f);
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
+    const int y = i / N, x = i % N;
+    const float2 o = a.O[static_cast<size_t>(py + y) * a.W + px + x];
+    psi[static_cast<size_t>(m) * K + i] = cmul(a.P[i], o);
+    const float q = o.x * o.x + o.y * o.y;
+    if (q > best) { best = q; bv = o; }
+  }
+  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
+  d = block_max<256>(d, sh);
+  if (threadIdx.x == 0) atomic_max_pos_double(omax_bits + m, d);
+}
+
+// modulus replacement on the cuFFT spectrum (1/N^2 folded in); 256 threads x
+// 4 elements per block, per-block error partials
+template <typename IT>
+__global__ void plain_modulus_kernel(GroupArgs a, int N, float2 *__restrict__ Psi) {
+  __shared__ double se[8], ss[8];
+  const int m = blockIdx.y, K = N * N;
+  const int f = a.members[m];
+  const IT *I = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * K;
+  const float invK = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
+  float e = 0.f, s = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int k = blockIdx.x * 1024 + r * 256 + threadIdx.x;
+    float In = ival(I[k]);
+    if (a.dark) In -= a.dark[k];
+    In = fmaxf(In, 0.f);
+    const float sq = sqrtf(In);
+    float2 v = Psi[static_cast<size_t>(m) * K + k];
+    const float a2 = v.x * v.x + v.y * v.y;
+    float amp;
+    if (a2 > 0.f) {
+      const float ia = rsqrtf(a2);
+      amp = a2 * ia;
+      v = cscale(v, sq * ia * invK);
+    } else {
+      amp = 0.f;
+      v = make_float2(sq * invK, 0.f);
+    }
+    Psi[static_cast<size_t>(m) * K + k] = v;
+    const float d = amp - sq;
+    e = fmaf(d, d, e);
+    s += In;
+  }
+  double de = warp_sum(static_cast<double>(e)), ds = warp_sum(static_cast<double>(s));
+  if ((threadIdx.x & 31) == 0) {
+    se[threadIdx.x >> 5] = de;
+    ss[threadIdx.x >> 5] = ds;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double te = 0.0, ts = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      te += se[w];
+      ts += ss[w];
+    }
+    a.err_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = te;
+    a.isum_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = ts;
+  }
+}
+
+// O patch update and probe partial from psi' (= inverse cuFFT output)
+__global__ void plain_update_kernel(GroupArgs a, int N, const float2 *__restrict__ psi1,
+                                    const unsigned long long *__restrict__ omax_bits) {
+  const int m = blockIdx.y, K = N * N;
+  const int f = a.members[m];
+  const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
+  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+  const double om = a.omax2_global ? *a.omax2_global
+                                   : __longlong_as_double(static_cast<long long>(omax_bits[m]));
+  const float ao = pm > 0.0 ? static_cast<float>(static_cast<double>(a.alpha) / pm) : 0.f;
+  const float bp = om > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om) : 0.f;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
+    const int y = i / N, x = i % N;
+    float2 *op = a.O + static_cast<size_t>(py + y) * a.W + px + x;
+    const float2 o = *op, p = a.P[i];
+    const float2 d = csub(psi1[static_cast<size_t>(m) * K + i], cmul(p, o));
+    const float2 uo = cmulc(p, d), up = cmulc(o, d);
+    *op = make_float2(fmaf(ao, uo.x, o.x), fmaf(ao, uo.y, o.y));
+    a.probe_part[static_cast<size_t>(m) * K + i] = cscale(up, bp);
+  }
+}
+
+// ---------------------------------------------------------------- mini-batch
+
+// accumulate conj(P) Delta / max|P|^2 into accO and the coverage count
+// (overlapping patches: float atomics, order-dependent rounding only)
+__global__ void mb_accumulate_kernel(GroupArgs a, int N, const float2 *__restrict__ psi1,
+                                     const unsigned long long *__restrict__ omax_bits,
+                                     float2 *__restrict__ accO, int *__restrict__ cnt) {
+  const int m = blockIdx.y, K = N * N;
+  const int f = a.members[m];
+  const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
+  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+  const double om = a.omax2_global ? *a.omax2_global
+                                   : __longlong_as_double(static_cast<long long>(omax_bits[m]));
+  const float ao = pm > 0.0 ? static_cast<float>(1.0 / pm) : 0.f;
+  const float bp = om > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om) : 0.f;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
+    const int y = i / N, x = i % N;
+    const size_t oi = static_cast<size_t>(py + y) * a.W + px + x;
+    const float2 o = a.O[oi], p = a.P[i];
+    const float2 d = csub(psi1[static_cast<size_t>(m) * K + i], cmul(p, o));
+    const float2 uo = cscale(cmulc(p, d), ao), up = cmulc(o, d);
+    atomicAdd(&accO[oi].x, uo.x);
+    atomicAdd(&accO[oi].y, uo.y);
+    atomicAdd(cnt + oi, 1);
+    a.probe_part[static_cast<size_t>(m) * K + i] = cscale(up, bp);
+  }
+}
+
+// O += alpha accO / cnt where cnt > 0; clears the accumulators
+__global__ void mb_apply_kernel(float2 *__restrict__ O, float2 *__restrict__ accO,
+                                int *__restrict__ cnt, long long n, float alpha) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = cnt[i];
+    if (c > 0) {
+      const float2 u = accO[i];
+      const float s = alpha / static_cast<float>(c);
+      float2 o = O[i];
+      o.x = fmaf(s, u.x, o.x);
+      o.y = fmaf(s, u.y, o.y);
+      O[i] = o;
+      accO[i] = make_float2(0.f, 0.f);
+      cnt[i] = 0;
+    }
+  }
+}
+
+__global__ void fill_kernel(float2 *__restrict__ p, long long n, float2 v) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+
+int grid_for(long long n, int nt, int cap) {
+  long long g = (n + nt - 1) / nt;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+}  // namespace
+
+cudaError_t launch_ingest(const void *raw, void *dst, int n, int N, int esize, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int cpr = N * esize / 16;
+  const long long total = static_cast<long long>(n) * N * cpr;
+  ingest_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>(
+      static_cast<const uint4 *>(raw), static_cast<uint4 *>(dst), n, N, cpr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st) {
+  fill_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t st) {
+  dark_ingest_kernel<<<(N * N + 255) / 256, 256, 0, st>>>(raw, dst, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, int N, float scale,
+                                unsigned long long *pmax2_next, cudaStream_t st) {
+  const int K = N * N;
+  probe_reduce_kernel<256><<<grid_for(K, 256, 152 * 4), 256, 0, st>>>(P, part, n_members, K, scale,
+                                                                       pmax2_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, cudaStream_t st) {
+  abs2_max_kernel<256><<<grid_for(K, 256, 152 * 2), 256, 0, st>>>(P, K, pmax2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_object_max(const float2 *O, long long n, double *out, unsigned long long *tmp,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  abs2_max_kernel<256><<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(O, n, tmp);
+  bits_to_double_kernel<<<1, 1, 0, st>>>(tmp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_error_reduce(const double *err_part, const double *isum_part, int n_frames,
+                                int stride, double *out, cudaStream_t st) {
+  error_reduce_kernel<1024><<<1, 1024, 0, st>>>(err_part, isum_part, n_frames, stride, out);
+  return cudaGetLastError();
+}
+
+int plain_err_stride(int N) { return N * N / 1024; }
+
+cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,
+                                cudaStream_t st) {
+  auto *bits = reinterpret_cast<unsigned long long *>(omax2);
+  cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * a.n_members, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N * N / 1024, a.n_members);
+  plain_gather_kernel<<<grid, 256, 0, st>>>(a, N, psi, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_modulus(const GroupArgs &a, int N, int itype, float2 *Psi,
+                                 cudaStream_t st) {
+  dim3 grid(N * N / 1024, a.n_members);
+  if (itype == 0) plain_modulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, Psi);
+  else if (itype == 1) plain_modulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, Psi);
+  else plain_modulus_kernel<float><<<grid, 256, 0, st>>>(a, N, Psi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_update(const GroupArgs &a, int N, const float2 *psi1, const double *omax2,
+                                cudaStream_t st) {
+  dim3 grid(N * N / 1024, a.n_members);
+  plain_update_kernel<<<grid, 256, 0, st>>>(a, N, psi1,
+                                            reinterpret_cast<const unsigned long long *>(omax2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
+                                 const double *omax2, float2 *accO, int *cnt, cudaStream_t st) {
+  dim3 grid(N * N / 1024, a.n_members);
+  mb_accumulate_kernel<<<grid, 256, 0, st>>>(
+      a, N, psi1, reinterpret_cast<const unsigned long long *>(omax2), accO, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
+                            cudaStream_t st) {
+  mb_apply_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(O, accO, cnt, n, alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace epie

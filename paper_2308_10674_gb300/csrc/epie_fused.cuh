@@ -1,0 +1,302 @@
+// epie_fused.cuh -- the fused ePIE position-update kernel.
+//
+// One thread-block cluster of CL CTAs owns one scan position of a group
+// (ePIE step, Maiden & Rodenburg 2009, as run by the paper's engine, Sec.
+// "ePIE Implementation"; alpha = beta = 1 in the paper):
+//
+//   phase 1  CTA c forms the exit wave psi = P . O_j on the column block
+//            [c N/CL, (c+1) N/CL) and transforms every column (FFT along y);
+//   swap     all-to-all transpose through distributed shared memory: CTA c
+//            now holds the row block [c N/CL, (c+1) N/CL) of the spectrum;
+//   phase 2  FFT along x, modulus replacement with sqrt(I) (intensity tile
+//            staged by a bulk TMA copy issued at kernel start, dark field
+//            subtracted, error terms summed), inverse FFT along x;
+//   swap     transpose back to column blocks;
+//   phase 3  inverse FFT along y -> psi', Delta = psi' - psi, object patch
+//            update with conj(P)/max|P|^2 (patches of a group are disjoint, so
+//            the writes never race) and the probe-update partial
+//            beta conj(O_old)/max|O_old|^2 Delta for the group reduction.
+//
+// For N <= 128 one CTA holds the whole frame (CL = 1) and the swaps are
+// plain shared-memory re-indexing.  Shared memory holds one tile per CTA,
+// the twiddle table, the intensity tile and a few reduction slots.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "epie_fft.cuh"
+#include "epie_internal.h"
+
+namespace epie {
+
+namespace cg = cooperative_groups;
+
+template <int N, int CL, int NT, typename IT>
+struct FusedCfg {
+  static constexpr int WC = N / CL;        // columns per CTA in phases 1 and 3
+  static constexpr int HR = N / CL;        // rows per CTA in phase 2
+  static constexpr int PB = N + N / 16;    // padded row pitch of the row tile
+  static constexpr int E = N * WC / NT;    // elements per thread, phases 1 and 3
+  static constexpr int NW = NT / 32;
+  static constexpr int SLAB =
+      CL == 1 ? N * PB : (N * WC > HR * PB ? N * WC : HR * PB);  // float2 elements
+  static constexpr size_t OFF_TW = sizeof(float2) * SLAB;
+  static constexpr size_t OFF_I = OFF_TW + sizeof(float2) * N;
+  static constexpr uint32_t I_BYTES = HR * N * sizeof(IT);
+  static constexpr size_t OFF_RED = (OFF_I + I_BYTES + 15) / 16 * 16;
+  static constexpr size_t OFF_BAR = OFF_RED + sizeof(double) * (2 * NW + 2);
+  static constexpr size_t SMEM = OFF_BAR + 16;
+  static_assert(E * NT == N * WC, "tile must split evenly over threads");
+  static_assert(I_BYTES % 16 == 0, "bulk copy size");
+  static_assert(OFF_I % 16 == 0, "bulk copy destination alignment");
+};
+
+template <int N, typename IT>
+struct ModReplace {
+  const IT *itile;     // HR x N intensities of this CTA's rows, FFT order
+  const float *dark;   // N x N FFT order or nullptr
+  int ky0;             // first spectrum row of the tile
+  float e, s;          // sum (|Psi| - sqrt I)^2, sum I (FP32 per thread)
+  __device__ __forceinline__ float2 operator()(int b, int kx, float2 v) {
+    float I = ival(itile[b * N + kx]);
+    if (dark) I -= __ldg(dark + (ky0 + b) * N + kx);
+    I = fmaxf(I, 0.f);
+    const float sq = sqrtf(I);
+    const float a2 = v.x * v.x + v.y * v.y;
+    constexpr float invK = 1.0f / (float(N) * float(N));
+    float2 out;
+    float amp;
+    if (a2 > 0.f) {
+      const float ia = rsqrtf(a2);
+      amp = a2 * ia;
+      const float r = sq * ia * invK;
+      out = make_float2(v.x * r, v.y * r);
+    } else {
+      amp = 0.f;
+      out = make_float2(sq * invK, 0.f);
+    }
+    const float d = amp - sq;
+    e = fmaf(d, d, e);
+    s += I;
+    return out;
+  }
+};
+
+template <int N, int CL, int NT, typename IT>
+__global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(GroupArgs a) {
+  using C = FusedCfg<N, CL, NT, IT>;
+  constexpr int WC = C::WC, HR = C::HR, PB = C::PB, E = C::E, NW = C::NW;
+  using ColA = ColAddr<CL == 1 ? PB : WC, CL == 1>;
+  using RowB = RowAddr<PB>;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2 *slab = reinterpret_cast<float2 *>(smem);
+  float2 *tw = reinterpret_cast<float2 *>(smem + C::OFF_TW);
+  IT *itile = reinterpret_cast<IT *>(smem + C::OFF_I);
+  double *red = reinterpret_cast<double *>(smem + C::OFF_RED);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int member = blockIdx.x / CL;
+  int crank = 0;
+  if constexpr (CL > 1) crank = static_cast<int>(cg::this_cluster().block_rank());
+  const int f = a.members[member];
+  const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
+  const IT *frame = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * N * N;
+
+  // intensity rows [crank*HR, +HR) of the frame: one bulk copy, waited on
+  // just before the modulus replacement
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, C::I_BYTES);
+    bulk_g2s(itile, frame + static_cast<size_t>(crank) * HR * N, C::I_BYTES, bar);
+  }
+  for (int m = tid; m < N; m += NT) tw[m] = a.twiddle[m];
+  if (blockIdx.x == 0 && tid == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
+
+  // ---------------------------------------------------------------- phase 1
+  const size_t orow = static_cast<size_t>(a.W);
+  float2 *Obase = a.O + static_cast<size_t>(py) * orow + px + crank * WC;
+  const float2 *Pbase = a.P + crank * WC;
+  float om = -1.f;
+  float2 omv = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+    const float2 p = Pbase[y * N + xl];
+    const float2 o = Obase[y * orow + xl];
+    const float q = o.x * o.x + o.y * o.y;
+    if (q > om) { om = q; omv = o; }
+    slab[ColA::at(xl, y)] = cmul(p, o);
+  }
+  __syncthreads();
+  fft_all<N, false, NT, WC, false, ColA>(slab, tw);
+
+  // max |O_old|^2 over the patch: FP32 comparison, FP64 value and reduction
+  double omax = warp_max(static_cast<double>(omv.x) * omv.x + static_cast<double>(omv.y) * omv.y);
+  if (lane == 0) red[2 + warp] = omax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = red[2];
+    for (int w = 1; w < NW; ++w) m = fmax(m, red[2 + w]);
+    red[0] = m;
+  }
+
+  if constexpr (CL > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();  // column transforms and red[0] of every CTA visible
+    constexpr int CH = HR * WC / 2;  // float4 per (peer, this CTA) block
+    float4 t4[E / 2];
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i) {
+      const int m = tid + i * NT, q = m / CH, off = m % CH;
+      const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(slab, q));
+      t4[i] = src[crank * CH + off];
+    }
+    double om_all = 0.0;
+    for (int q = 0; q < CL; ++q) om_all = fmax(om_all, *cluster.map_shared_rank(red, q));
+    cluster.sync();  // all remote reads done before the tile is overwritten
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i) {
+      const int m = tid + i * NT, q = m / CH, off = m % CH;
+      const int e0 = 2 * off, yl = e0 / WC, x = q * WC + e0 % WC;
+      slab[RowB::at(yl, x)] = make_float2(t4[i].x, t4[i].y);
+      slab[RowB::at(yl, x + 1)] = make_float2(t4[i].z, t4[i].w);
+    }
+    omax = om_all;
+    __syncthreads();
+  } else {
+    __syncthreads();  // red[0] written by thread 0
+    omax = red[0];
+  }
+
+  // ---------------------------------------------------------------- phase 2
+  bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+  if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
+  ModReplace<N, IT> mod{itile, a.dark, crank * HR, 0.f, 0.f};
+  fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
+  {
+    double e = warp_sum(static_cast<double>(mod.e));
+    double s = warp_sum(static_cast<double>(mod.s));
+    if (lane == 0) {
+      red[2 + warp] = e;
+      red[2 + NW + warp] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double es = 0.0, ss = 0.0;
+      for (int w = 0; w < NW; ++w) {
+        es += red[2 + w];
+        ss += red[2 + NW + w];
+      }
+      a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = es;
+      a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] = ss;
+    }
+  }
+
+  if constexpr (CL > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    float2 t2[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+      const float2 *src = cluster.map_shared_rank(slab, y / HR);
+      t2[i] = src[RowB::at(y % HR, crank * WC + xl)];
+    }
+    cluster.sync();
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+      slab[ColA::at(xl, y)] = t2[i];
+    }
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------------- phase 3
+  fft_all<N, true, NT, WC, false, ColA>(slab, tw);
+
+  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+  const double om_used = a.omax2_global ? *a.omax2_global : omax;
+  const float ao = pm > 0.0 ? static_cast<float>(static_cast<double>(a.alpha) / pm) : 0.f;
+  const float bp = om_used > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om_used) : 0.f;
+  float2 *part = a.probe_part + static_cast<size_t>(member) * N * N + crank * WC;
+  if (ok && a.accO == nullptr) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+      const float2 psi1 = slab[ColA::at(xl, y)];
+      const float2 p = Pbase[y * N + xl];
+      const float2 o = Obase[y * orow + xl];
+      const float2 d = csub(psi1, cmul(p, o));
+      const float2 uo = cmulc(p, d);  // conj(P) Delta
+      const float2 up = cmulc(o, d);  // conj(O_old) Delta
+      Obase[y * orow + xl] = make_float2(fmaf(ao, uo.x, o.x), fmaf(ao, uo.y, o.y));
+      part[y * N + xl] = cscale(up, bp);
+    }
+  } else if (ok) {
+    // mini-batch: patches of a batch may overlap; the object moves once per
+    // batch by the count-normalised sum, applied by a separate kernel
+    const float inv_pm = pm > 0.0 ? static_cast<float>(1.0 / pm) : 0.f;
+    const size_t obase = static_cast<size_t>(py) * orow + px + crank * WC;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+      const float2 psi1 = slab[ColA::at(xl, y)];
+      const float2 p = Pbase[y * N + xl];
+      const float2 o = Obase[y * orow + xl];
+      const float2 d = csub(psi1, cmul(p, o));
+      const float2 uo = cscale(cmulc(p, d), inv_pm);
+      const size_t oi = obase + y * orow + xl;
+      atomicAdd(&a.accO[oi].x, uo.x);
+      atomicAdd(&a.accO[oi].y, uo.y);
+      atomicAdd(a.cnt + oi, 1);
+      part[y * N + xl] = cscale(cmulc(o, d), bp);
+    }
+  } else {
+    // the copy never arrived: give it one more bounded wait before exiting
+    mbar_wait_bounded(bar, 0, 100000000ull);
+  }
+}
+
+template <int N, int CL, int NT, typename IT>
+cudaError_t launch_fused_t(const GroupArgs &a, cudaStream_t st) {
+  using C = FusedCfg<N, CL, NT, IT>;
+  auto kern = epie_fused_kernel<N, CL, NT, IT>;
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(C::SMEM));
+    if (e != cudaSuccess) return e;
+    if (CL > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    configured[dev] = true;
+  }
+  if (a.n_members <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(a.n_members * CL), 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (CL > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace epie

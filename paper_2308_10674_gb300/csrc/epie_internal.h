@@ -1,0 +1,79 @@
+// epie_internal.h -- declarations shared by the host scheduler (epie_abi.cpp)
+// and the kernels (epie_fused_*.cu, epie_aux.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace epie {
+
+// Arguments of one group launch of the fused ePIE kernel (and of the plain
+// path's per-group kernels).  All pointers are device pointers.
+struct GroupArgs {
+  float2 *O;                  // object, H x W, row-major
+  int W;                      // object row pitch (elements)
+  const float2 *P;            // probe at group start, N x N
+  const void *frames;         // device frame set [capacity][N][N], FFT order
+  const float *dark;          // N x N FFT order, or nullptr
+  const int32_t *pos;         // [capacity][2] patch top-left (y, x)
+  const int32_t *members;     // frame ids of this group
+  int n_members;
+  float2 *probe_part;         // [n_members][N][N] probe-update partials
+  double *err_part;           // [capacity][err_stride] sum (|Psi|-sqrt I)^2
+  double *isum_part;          // [capacity][err_stride] sum I
+  int err_stride;             // partial slots per frame
+  const unsigned long long *pmax2;  // bits of max|P|^2 (double) of this group
+  unsigned long long *pmax2_clear;  // slot to zero for the next group's max
+  const double *omax2_global; // max|O|^2 over the object, or nullptr (patch max)
+  const float2 *twiddle;      // N entries exp(-2 pi i m / N)
+  float alpha, beta;
+  int *err_flag;              // device status word (bounded waits)
+  float2 *accO;               // mini-batch: object-update accumulator (H x W) or nullptr
+  int *cnt;                   // mini-batch: per-pixel count of covering patches
+};
+
+// error-flag bits written by kernels
+enum : int { FLAG_TMA_TIMEOUT = 1 };
+
+// fused kernel: one group, dispatch on N and intensity type
+cudaError_t launch_fused(int N, int itype, const GroupArgs &a, cudaStream_t st);
+// CTAs per frame used by the fused kernel for this N (error slots per frame)
+int fused_ctas_per_frame(int N);
+// dynamic shared memory of the fused kernel (for diagnostics)
+size_t fused_smem_bytes(int N, int itype);
+
+// probe update after a group: P += scale * sum_m part[m]; writes bits of
+// max|P|^2 (double) into *pmax2_next (must be zero on entry)
+cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, int N, float scale,
+                                unsigned long long *pmax2_next, cudaStream_t st);
+// max|P|^2 of the probe into *pmax2 (zeroed by the kernel's caller)
+cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, cudaStream_t st);
+// max|O|^2 over the object into *out (double)
+cudaError_t launch_object_max(const float2 *O, long long n, double *out, unsigned long long *tmp,
+                              cudaStream_t st);
+// sweep error: E = sum e / sum s over frames [0, n_frames), fixed order
+cudaError_t launch_error_reduce(const double *err_part, const double *isum_part, int n_frames,
+                                int stride, double *out, cudaStream_t st);
+// live ingest: raw DC-centred frames -> device set in FFT order (ifftshift)
+cudaError_t launch_ingest(const void *raw, void *dst, int n, int N, int esize, cudaStream_t st);
+// p[0..n) = v
+cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st);
+// dark field: DC-centred float -> FFT order
+cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t st);
+
+// plain unfused path pieces
+cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,
+                                cudaStream_t st);
+cudaError_t launch_plain_modulus(const GroupArgs &a, int N, int itype, float2 *Psi,
+                                 cudaStream_t st);
+cudaError_t launch_plain_update(const GroupArgs &a, int N, const float2 *psi1,
+                                const double *omax2, cudaStream_t st);
+int plain_err_stride(int N);
+
+// mini-batch path: accumulate object deltas / counts, then apply
+cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
+                                 const double *omax2, float2 *accO, int *cnt, cudaStream_t st);
+cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
+                            cudaStream_t st);
+
+}  // namespace epie

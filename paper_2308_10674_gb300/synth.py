@@ -235,8 +235,30 @@ def config0(seed=0, photons=1e6, noise=True):
                 dark=None, clamped=clamped, photons=photons, seed=seed)
 
 
+_W = {}
+
+
+def _init_worker(O, P, D):
+    _W["O"], _W["P"], _W["D"] = O, P, D
+
+
+def _frames_chunk(args):
+    """Frames [a, b) of a scan; noise drawn from a substream keyed by the chunk
+    index, so the result does not depend on how chunks are spread over workers."""
+    pos, seed, chunk, noise = args
+    lam = far_field_intensity(_W["O"], _W["P"], pos, dtype=np.complex64)
+    if _W["D"] is not None:
+        lam = lam + _W["D"][None].astype(np.float64)
+    if noise:
+        return poisson_u16(lam, substream(seed, 1000 + chunk))
+    return lam.astype(np.float32), 0.0
+
+
+LIVE_CHUNK = 250
+
+
 def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, noise=True,
-              dark=True, n_frames=None, batch=128):
+              dark=True, n_frames=None, workers=1):
     """Beamline-like live workload: N x N uint16 frames on a Fermat spiral.
 
     geometry "A": step = 0.35 x probe FWHM (median nearest-neighbour distance),
@@ -244,8 +266,10 @@ def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, nois
     1400^2 (step about 9.7 px).  Probe radius and apodisation are scaled so
     that |P|^2 has the given FWHM; object phase smoothing scales with it.
     `n_frames` simulates only the first n_frames positions (the geometry is
-    still that of the full scan)."""
-    rng_obj, rng_noise, rng_dark = substream(seed, 11), substream(seed, 13), substream(seed, 14)
+    still that of the full scan).  `workers` > 1 simulates chunks of frames
+    in a process pool (spawned, so it is safe after CUDA initialisation);
+    the frames are identical for any worker count."""
+    rng_obj, rng_dark = substream(seed, 11), substream(seed, 14)
     R = probe_radius_for_fwhm(N, fwhm)
     sig_ap = 3.0 * R / 20.0
     if geometry == "A":
@@ -260,21 +284,24 @@ def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, nois
     pos = tl[:m]
     P_true = scale_probe_to_photons(O_true, make_probe(N, R, sig_ap), pos[: min(m, 500)], photons)
     D = dark_field(N, photons, rng_dark) if dark else None
-    frames = np.empty((m, N, N), np.uint16 if noise else np.float32)
-    clamped = 0.0
-    for a in range(0, m, batch):
-        b = min(m, a + batch)
-        lam = far_field_intensity(O_true, P_true, pos[a:b], dtype=np.complex64)
-        if D is not None:
-            lam = lam + D[None].astype(np.float64)
-        if noise:
-            frames[a:b], cf = poisson_u16(lam, rng_noise)
-            clamped += cf * (b - a)
-        else:
-            frames[a:b] = lam
+    jobs = [(pos[a:min(m, a + LIVE_CHUNK)], seed, a // LIVE_CHUNK, noise)
+            for a in range(0, m, LIVE_CHUNK)]
+    O32, P32 = O_true.astype(np.complex64), P_true.astype(np.complex64)
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(min(workers, len(jobs)), initializer=_init_worker,
+                      initargs=(O32, P32, D)) as pool:
+            parts = pool.map(_frames_chunk, jobs)
+    else:
+        _init_worker(O32, P32, D)
+        parts = [_frames_chunk(j) for j in jobs]
+    frames = (np.concatenate([p[0] for p in parts]) if parts else
+              np.empty((0, N, N), np.uint16 if noise else np.float32))
+    clamped = sum(p[1] * len(j[0]) for p, j in zip(parts, jobs)) / max(m, 1)
     return dict(N=N, H=H, W=W, pos=pos, frames=frames, O_true=O_true, P_true=P_true,
                 O0=np.ones((H, W), np.complex128), P0=initial_probe(N, R, sig_ap, photons),
-                dark=D, clamped=clamped / max(m, 1), photons=photons, seed=seed,
+                dark=D, clamped=clamped, photons=photons, seed=seed,
                 geometry=geometry, spiral_c=c, probe_radius=R, n_total=n)
 
 

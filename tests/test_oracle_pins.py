@@ -86,6 +86,9 @@ def test_prepare_intensity_shift_dark_and_types(orc):
     Ih = orc.prepare_intensity(h)[0]
     assert Ih[0, 0] == 65504.0 and Ih[0, 1] == 2.0 ** -24 and Ih[0, 2] == 0.0 and Ih[0, 3] == 2048.0
     f = np.arange(N * N, dtype=np.float32).reshape(1, N, N) + 0.25
+    fn = f.copy()
+    fn[0, N // 2, N // 2] = np.nan
+    assert orc.prepare_intensity(fn)[0][0, 0] == 0.0  # NaN clamps to 0 like negatives
     If = orc.prepare_intensity(f)[0]
     assert np.array_equal(If, np.fft.ifftshift(f[0]).astype(np.float64))
 
