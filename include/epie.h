@@ -215,6 +215,45 @@ EPIE_API int epie_launch_count(epie_t h, int64_t *total);
 EPIE_API int epie_set_kernel_timing(epie_t h, int32_t on);
 EPIE_API int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t *frames);
 
+/* One ePIE group update on caller-owned device buffers, allocating no device
+ * memory.  The paper has no counterpart: this entry point serves callers that
+ * cannot allocate device memory themselves or through the engine -- a
+ * detector or acquisition framework that owns the GPU's memory and lends out
+ * fixed buffers, or a live loop that must not take the device-wide
+ * synchronisation of cudaMalloc / cudaFree.
+ *
+ * It runs the same step as epie_iterate does for one group (one colour
+ * class): every member's exit wave, far field, modulus replacement, object
+ * patch update with the probe at group start, then the probe update by the
+ * mean (probe_mean != 0) or the sum of the members' probe updates.
+ *   object   device, obj_h*obj_w complex float32 (updated in place)
+ *   probe    device, N*N complex float32 (updated in place)
+ *   frames   device, n_frames*N*N intensities of type intensity_dtype in FFT
+ *            order (zero frequency at index [0,0], not DC-centred)
+ *   pos      device, n_frames*(y, x) int32 patch top-left positions
+ *   members  device, n_members frame ids of the group; their patches must be
+ *            pairwise disjoint when n_members > 1
+ *   dark     device, N*N float32 in FFT order, or NULL
+ *   err_terms host, 2 doubles receiving sum (|Psi| - sqrt I)^2 and sum I over
+ *            the group, or NULL; when given, the call waits for the step
+ *   stream   cudaStream_t (NULL: the legacy default stream)
+ * All scratch lives in one file-scope device array of about 36 MiB that every
+ * GPU loading the library holds until exit; calls share it and it keeps the
+ * last call's contents, so calls that overlap on the GPU (other streams,
+ * other host threads) race.  Limits (scratch size): n_frames <= 16384,
+ * n_members <= 1024, 256, 64, 16 for N = 64, 128, 256, 512; beyond them the
+ * call returns EPIE_EINVAL without launching anything.  Member ids,
+ * positions and disjointness are checked on the device before the step
+ * (EPIE_EINVAL / EPIE_ERANGE).  The first call on a device looks the array's
+ * device address up and uploads the twiddle tables; make that first call
+ * before any stream capture.  On failure epie_error(NULL) holds the reason. */
+EPIE_API int epie_group_step_static(int32_t N, int32_t intensity_dtype, float *object,
+                                    int32_t obj_h, int32_t obj_w, float *probe,
+                                    const void *frames, int32_t n_frames, const int32_t *pos,
+                                    const int32_t *members, int32_t n_members,
+                                    const float *dark, float alpha, float beta,
+                                    int32_t probe_mean, double *err_terms, void *stream);
+
 /* Message of the handle's last error (or of the last failed epie_init in
  * this thread when h is NULL).  Valid until the next call on the handle. */
 EPIE_API const char *epie_error(epie_t h);

@@ -73,6 +73,8 @@ def lib():
         L.epie_set_kernel_timing.argtypes = [H, i32]
         L.epie_kernel_timing.argtypes = [H, C.POINTER(i64), C.POINTER(C.c_double),
                                          C.POINTER(i64)]
+        L.epie_group_step_static.argtypes = [i32, i32, vp, i32, i32, vp, vp, i32, vp, vp, i32,
+                                             vp, C.c_float, C.c_float, i32, vp, vp]
         L.epie_error.argtypes = [H]
         L.epie_error.restype = C.c_char_p
         L.epie_destroy.argtypes = [H]
@@ -232,6 +234,23 @@ def epie_kernel_timing(h):
     n, ms, f = C.c_int64(), C.c_double(), C.c_int64()
     _check(h, lib().epie_kernel_timing(h, C.byref(n), C.byref(ms), C.byref(f)))
     return n.value, ms.value, f.value
+
+
+def epie_group_step_static(N, intensity_dtype, object_ptr, obj_h, obj_w, probe_ptr, frames_ptr,
+                           n_frames, pos_ptr, members_ptr, n_members, dark_ptr=None, alpha=1.0,
+                           beta=1.0, probe_mean=True, want_err=True, stream=None):
+    """One group update on caller-owned device buffers (integer device
+    addresses), allocating no device memory.  Returns the group's
+    (sum (|Psi| - sqrt I)^2, sum I) when want_err."""
+    err = np.zeros(2, np.float64)
+    rc = lib().epie_group_step_static(
+        N, intensity_dtype, C.c_void_p(object_ptr), obj_h, obj_w, C.c_void_p(probe_ptr),
+        C.c_void_p(frames_ptr), n_frames, C.c_void_p(pos_ptr), C.c_void_p(members_ptr), n_members,
+        C.c_void_p(dark_ptr) if dark_ptr else None, alpha, beta, 1 if probe_mean else 0,
+        _p(err) if want_err else None, C.c_void_p(stream) if stream else None)
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
+    return err
 
 
 # --------------------------------------------------------------------------- convenience

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libepie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["epie_abi.cpp", "epie_dispatch.cu", "epie_aux.cu", "epie_fused_64.cu",
-           "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu"]
+           "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu"]
 
 
 def nvcc() -> str:

@@ -54,6 +54,11 @@ size_t esize_of(int dtype) { return dtype == EPIE_F32 ? 4 : 2; }
 
 }  // namespace
 
+namespace epie {
+// the calling thread's epie_error(NULL) message
+std::string &init_error_sink() { return g_init_error; }
+}  // namespace epie
+
 // ------------------------------------------------------------------ handle
 
 struct epie_ctx {
