@@ -13,6 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libepie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# extra nvcc flags (e.g. -DEPIE_CTAS_256=4 to build another cluster shape)
+EXTRA = os.environ.get("EPIE_NVCC_FLAGS", "").split()
 SOURCES = ["epie_abi.cpp", "epie_dispatch.cu", "epie_aux.cu", "epie_fused_64.cu",
            "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu"]
 
@@ -41,7 +43,7 @@ def _compile(src: str, verbose: bool) -> str:
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "-c", path, "-o", obj]
+           "-Xcompiler", "-fvisibility=hidden", *EXTRA, "-c", path, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -57,28 +57,61 @@ __global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restr
 
 // ---------------------------------------------------------------- probe
 
-// P += scale * sum_{m < n_members} part[m] (members in order), then the
-// FP64 max|P|^2 of the new probe (FP32 comparison picks the element).
-template <int NT>
-__global__ void __launch_bounds__(NT) probe_reduce_kernel(float2 *__restrict__ P,
+// P += scale * sum_{m < n_members} part[m], then the FP64 max|P|^2 of the
+// new probe (FP32 comparison picks the element).  A block of 32 x 8 threads
+// covers 64 complex elements (two per thread, 16-byte loads); thread row r
+// sums members r, r+8, ... in order and the 8 row sums are added in row
+// order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ P,
                                                           const float2 *__restrict__ part,
                                                           int n_members, int K, float scale,
                                                           unsigned long long *pmax2_next) {
-  __shared__ double sh[NT / 32];
+  __shared__ float4 acc_sh[8][32];
+  __shared__ double sh[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float best = -1.f;
   float2 bv = make_float2(0.f, 0.f);
-  for (int i = blockIdx.x * NT + threadIdx.x; i < K; i += gridDim.x * NT) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m = 0; m < n_members; ++m) acc = cadd(acc, part[static_cast<size_t>(m) * K + i]);
-    float2 p = P[i];
-    p.x = fmaf(scale, acc.x, p.x);
-    p.y = fmaf(scale, acc.y, p.y);
-    P[i] = p;
-    const float q = p.x * p.x + p.y * p.y;
-    if (q > best) { best = q; bv = p; }
+  for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
+    const int i = base + 2 * tx;  // K is a multiple of 64
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int m = ty;
+    for (; m + 24 < n_members; m += 32) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i);
+      const float4 a1 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 8) * K + i);
+      const float4 a2 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 16) * K + i);
+      const float4 a3 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 24) * K + i);
+      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+      acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
+      acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
+      acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
+    }
+    for (; m < n_members; m += 8) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i);
+      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+    }
+    acc_sh[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0) {
+      float4 t = acc_sh[0][tx];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) {
+        const float4 u = acc_sh[r][tx];
+        t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+      }
+      float4 p = *reinterpret_cast<float4 *>(P + i);
+      p.x = fmaf(scale, t.x, p.x);
+      p.y = fmaf(scale, t.y, p.y);
+      p.z = fmaf(scale, t.z, p.z);
+      p.w = fmaf(scale, t.w, p.w);
+      *reinterpret_cast<float4 *>(P + i) = p;
+      const float q0 = p.x * p.x + p.y * p.y, q1 = p.z * p.z + p.w * p.w;
+      if (q0 > best) { best = q0; bv = make_float2(p.x, p.y); }
+      if (q1 > best) { best = q1; bv = make_float2(p.z, p.w); }
+    }
+    __syncthreads();
   }
   double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
-  d = block_max<NT>(d, sh);
+  d = block_max<256>(d, sh);
   if (threadIdx.x == 0) atomic_max_pos_double(pmax2_next, d);
 }
 
@@ -312,8 +345,8 @@ cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t
 cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, int N, float scale,
                                 unsigned long long *pmax2_next, cudaStream_t st) {
   const int K = N * N;
-  probe_reduce_kernel<256><<<grid_for(K, 256, 152 * 4), 256, 0, st>>>(P, part, n_members, K, scale,
-                                                                       pmax2_next);
+  probe_reduce_kernel<<<grid_for(K, 64, 152 * 4), 256, 0, st>>>(P, part, n_members, K, scale,
+                                                                 pmax2_next);
   return cudaGetLastError();
 }
 

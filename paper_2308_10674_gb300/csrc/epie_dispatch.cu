@@ -24,10 +24,10 @@ cudaError_t launch_fused(int N, int itype, const GroupArgs &a, cudaStream_t st) 
 
 int fused_ctas_per_frame(int N) {
   switch (N) {
-    case 64: return 1;
-    case 128: return 2;
-    case 256: return 8;
-    case 512: return 16;
+    case 64: return EPIE_CTAS_64;
+    case 128: return EPIE_CTAS_128;
+    case 256: return EPIE_CTAS_256;
+    case 512: return EPIE_CTAS_512;
     default: return 0;
   }
 }

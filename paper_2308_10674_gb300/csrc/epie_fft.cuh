@@ -297,6 +297,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// L2 policy for data read once per sweep (the streamed frame set): evict first
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// as bulk_g2s, with an L2 cache policy for the source
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -328,6 +343,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// lane holding the largest q (FP32 comparison) hands its (re, im) to every lane
+__device__ __forceinline__ float2 warp_argmax_f(float q, float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float q2 = __shfl_xor_sync(0xffffffffu, q, o);
+    const float vx = __shfl_xor_sync(0xffffffffu, v.x, o);
+    const float vy = __shfl_xor_sync(0xffffffffu, v.y, o);
+    if (q2 > q) {
+      q = q2;
+      v = make_float2(vx, vy);
+    }
+  }
   return v;
 }
 __device__ __forceinline__ double warp_max(double v) {

@@ -31,6 +31,21 @@ namespace epie {
 
 namespace cg = cooperative_groups;
 
+// Phase clocks for profiling builds only (-DEPIE_PHASE_CLOCKS): thread 0 of
+// each CTA records clock64() at the phase boundaries; normal builds compile
+// the markers to nothing.
+#ifdef EPIE_PHASE_CLOCKS
+static __device__ long long g_phase_clocks[4096][16];
+#define EPIE_PHASE(k)                                                        \
+  do {                                                                       \
+    if (threadIdx.x == 0 && blockIdx.x < 4096) g_phase_clocks[blockIdx.x][k] = clock64(); \
+  } while (0)
+#else
+#define EPIE_PHASE(k) \
+  do {                \
+  } while (0)
+#endif
+
 template <int N, int CL, int NT, typename IT>
 struct FusedCfg {
   static constexpr int WC = N / CL;        // columns per CTA in phases 1 and 3
@@ -41,26 +56,24 @@ struct FusedCfg {
   static constexpr int SLAB =
       CL == 1 ? N * PB : (N * WC > HR * PB ? N * WC : HR * PB);  // float2 elements
   static constexpr size_t OFF_TW = sizeof(float2) * SLAB;
-  static constexpr size_t OFF_I = OFF_TW + sizeof(float2) * N;
-  static constexpr uint32_t I_BYTES = HR * N * sizeof(IT);
-  static constexpr size_t OFF_RED = (OFF_I + I_BYTES + 15) / 16 * 16;
+  static constexpr size_t OFF_I = OFF_TW + sizeof(float2) * N;  // float I_eff tile
+  static constexpr uint32_t I_BYTES = HR * N * sizeof(IT);        // raw tile (bulk copy)
+  static constexpr uint32_t IF_BYTES = HR * N * sizeof(float);
+  static constexpr size_t OFF_IRAW = OFF_I + IF_BYTES - I_BYTES;  // raw tile at the top
+  static constexpr size_t OFF_RED = (OFF_I + IF_BYTES + 15) / 16 * 16;
   static constexpr size_t OFF_BAR = OFF_RED + sizeof(double) * (2 * NW + 2);
   static constexpr size_t SMEM = OFF_BAR + 16;
   static_assert(E * NT == N * WC, "tile must split evenly over threads");
   static_assert(I_BYTES % 16 == 0, "bulk copy size");
-  static_assert(OFF_I % 16 == 0, "bulk copy destination alignment");
+  static_assert(OFF_IRAW % 16 == 0, "bulk copy destination alignment");
 };
 
-template <int N, typename IT>
+template <int N>
 struct ModReplace {
-  const IT *itile;     // HR x N intensities of this CTA's rows, FFT order
-  const float *dark;   // N x N FFT order or nullptr
-  int ky0;             // first spectrum row of the tile
+  const float *itile;  // HR x N intensities max(I - dark, 0) of this CTA's rows
   float e, s;          // sum (|Psi| - sqrt I)^2, sum I (FP32 per thread)
   __device__ __forceinline__ float2 operator()(int b, int kx, float2 v) {
-    float I = ival(itile[b * N + kx]);
-    if (dark) I -= __ldg(dark + (ky0 + b) * N + kx);
-    I = fmaxf(I, 0.f);
+    const float I = itile[b * N + kx];
     const float sq = sqrtf(I);
     const float a2 = v.x * v.x + v.y * v.y;
     constexpr float invK = 1.0f / (float(N) * float(N));
@@ -82,8 +95,14 @@ struct ModReplace {
   }
 };
 
+// resident CTAs per SM the register budget is sized for
+template <int CL, int NT>
+constexpr int fused_min_blocks() {
+  return CL == 1 ? 2 : (1024 / NT > 1 ? 1024 / NT : 1);
+}
+
 template <int N, int CL, int NT, typename IT>
-__global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_kernel(GroupArgs a) {
   using C = FusedCfg<N, CL, NT, IT>;
   constexpr int WC = C::WC, HR = C::HR, PB = C::PB, E = C::E, NW = C::NW;
   using ColA = ColAddr<CL == 1 ? PB : WC, CL == 1>;
@@ -92,11 +111,13 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   extern __shared__ __align__(128) unsigned char smem[];
   float2 *slab = reinterpret_cast<float2 *>(smem);
   float2 *tw = reinterpret_cast<float2 *>(smem + C::OFF_TW);
-  IT *itile = reinterpret_cast<IT *>(smem + C::OFF_I);
+  float *itile = reinterpret_cast<float *>(smem + C::OFF_I);
+  IT *iraw = reinterpret_cast<IT *>(smem + C::OFF_IRAW);
   double *red = reinterpret_cast<double *>(smem + C::OFF_RED);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  EPIE_PHASE(0);
   const int member = blockIdx.x / CL;
   int crank = 0;
   if constexpr (CL > 1) crank = static_cast<int>(cg::this_cluster().block_rank());
@@ -112,8 +133,10 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   }
   __syncthreads();
   if (tid == 0) {
+    // the frame is read once per sweep: keep it from evicting the object
     mbar_arrive_expect_tx(bar, C::I_BYTES);
-    bulk_g2s(itile, frame + static_cast<size_t>(crank) * HR * N, C::I_BYTES, bar);
+    bulk_g2s_hint(iraw, frame + static_cast<size_t>(crank) * HR * N, C::I_BYTES, bar,
+                  l2_evict_first_policy());
   }
   for (int m = tid; m < N; m += NT) tw[m] = a.twiddle[m];
   if (blockIdx.x == 0 && tid == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
@@ -124,20 +147,33 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   const float2 *Pbase = a.P + crank * WC;
   float om = -1.f;
   float2 omv = make_float2(0.f, 0.f);
+  constexpr int EB = E >= 8 ? 8 : E;  // loads issued together (one latency per batch)
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
-    const float2 p = Pbase[y * N + xl];
-    const float2 o = Obase[y * orow + xl];
-    const float q = o.x * o.x + o.y * o.y;
-    if (q > om) { om = q; omv = o; }
-    slab[ColA::at(xl, y)] = cmul(p, o);
+  for (int i0 = 0; i0 < E; i0 += EB) {
+    float2 pv[EB], ov[EB];
+#pragma unroll
+    for (int i = 0; i < EB; ++i) {
+      const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+      pv[i] = __ldg(Pbase + y * N + xl);
+      ov[i] = Obase[y * orow + xl];
+    }
+#pragma unroll
+    for (int i = 0; i < EB; ++i) {
+      const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+      const float q = ov[i].x * ov[i].x + ov[i].y * ov[i].y;
+      if (q > om) { om = q; omv = ov[i]; }
+      slab[ColA::at(xl, y)] = cmul(pv[i], ov[i]);
+    }
   }
   __syncthreads();
+  EPIE_PHASE(1);
   fft_all<N, false, NT, WC, false, ColA>(slab, tw);
+  EPIE_PHASE(2);
 
-  // max |O_old|^2 over the patch: FP32 comparison, FP64 value and reduction
-  double omax = warp_max(static_cast<double>(omv.x) * omv.x + static_cast<double>(omv.y) * omv.y);
+  // max |O_old|^2 over the patch: FP32 comparisons pick the element, its
+  // square is formed in FP64 and the maximum over warps taken in FP64
+  omv = warp_argmax_f(om, omv);
+  double omax = static_cast<double>(omv.x) * omv.x + static_cast<double>(omv.y) * omv.y;
   if (lane == 0) red[2 + warp] = omax;
   __syncthreads();
   if (tid == 0) {
@@ -149,6 +185,7 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   if constexpr (CL > 1) {
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();  // column transforms and red[0] of every CTA visible
+  EPIE_PHASE(3);
     constexpr int CH = HR * WC / 2;  // float4 per (peer, this CTA) block
     float4 t4[E / 2];
 #pragma unroll
@@ -159,6 +196,7 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
     }
     double om_all = 0.0;
     for (int q = 0; q < CL; ++q) om_all = fmax(om_all, *cluster.map_shared_rank(red, q));
+  EPIE_PHASE(4);
     cluster.sync();  // all remote reads done before the tile is overwritten
 #pragma unroll
     for (int i = 0; i < E / 2; ++i) {
@@ -169,6 +207,7 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
     }
     omax = om_all;
     __syncthreads();
+  EPIE_PHASE(5);
   } else {
     __syncthreads();  // red[0] written by thread 0
     omax = red[0];
@@ -177,14 +216,34 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   // ---------------------------------------------------------------- phase 2
   bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
-  ModReplace<N, IT> mod{itile, a.dark, crank * HR, 0.f, 0.f};
-  fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
   {
-    double e = warp_sum(static_cast<double>(mod.e));
-    double s = warp_sum(static_cast<double>(mod.s));
+    // intensity tile -> float max(I - dark, 0), in place: the raw tile sits
+    // at the top of the float tile, so every raw value is read (and the dark
+    // field fetched with one latency) before any float is written
+    constexpr int EI = HR * N / NT;
+    float iv[EI];
+#pragma unroll
+    for (int i = 0; i < EI; ++i) iv[i] = ival(iraw[tid + i * NT]);
+    if (a.dark) {
+      const float *dk = a.dark + crank * HR * N;
+#pragma unroll
+      for (int i = 0; i < EI; ++i) iv[i] -= __ldg(dk + tid + i * NT);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < EI; ++i) itile[tid + i * NT] = fmaxf(iv[i], 0.f);
+    // the first row pass's barrier orders these writes before the modulus
+  }
+  ModReplace<N> mod{itile, 0.f, 0.f};
+  EPIE_PHASE(6);
+  fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
+  EPIE_PHASE(7);
+  {
+    // FP32 within a warp, FP64 across warps, CTAs and frames
+    const float e = warp_sum_f(mod.e), s = warp_sum_f(mod.s);
     if (lane == 0) {
-      red[2 + warp] = e;
-      red[2 + NW + warp] = s;
+      red[2 + warp] = static_cast<double>(e);
+      red[2 + NW + warp] = static_cast<double>(s);
     }
     __syncthreads();
     if (tid == 0) {
@@ -197,10 +256,12 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
       a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] = ss;
     }
   }
+  EPIE_PHASE(8);
 
   if constexpr (CL > 1) {
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();
+    EPIE_PHASE(9);
     float2 t2[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -208,6 +269,7 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
       const float2 *src = cluster.map_shared_rank(slab, y / HR);
       t2[i] = src[RowB::at(y % HR, crank * WC + xl)];
     }
+  EPIE_PHASE(10);
     cluster.sync();
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -215,10 +277,12 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
       slab[ColA::at(xl, y)] = t2[i];
     }
     __syncthreads();
+  EPIE_PHASE(11);
   }
 
   // ---------------------------------------------------------------- phase 3
   fft_all<N, true, NT, WC, false, ColA>(slab, tw);
+  EPIE_PHASE(12);
 
   const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
   const double om_used = a.omax2_global ? *a.omax2_global : omax;
@@ -227,16 +291,25 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
   float2 *part = a.probe_part + static_cast<size_t>(member) * N * N + crank * WC;
   if (ok && a.accO == nullptr) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
-      const float2 psi1 = slab[ColA::at(xl, y)];
-      const float2 p = Pbase[y * N + xl];
-      const float2 o = Obase[y * orow + xl];
-      const float2 d = csub(psi1, cmul(p, o));
-      const float2 uo = cmulc(p, d);  // conj(P) Delta
-      const float2 up = cmulc(o, d);  // conj(O_old) Delta
-      Obase[y * orow + xl] = make_float2(fmaf(ao, uo.x, o.x), fmaf(ao, uo.y, o.y));
-      part[y * N + xl] = cscale(up, bp);
+    for (int i0 = 0; i0 < E; i0 += EB) {
+      // loads of a batch before its stores (the stores could alias them)
+      float2 pv[EB], ov[EB];
+#pragma unroll
+      for (int i = 0; i < EB; ++i) {
+        const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+        pv[i] = __ldg(Pbase + y * N + xl);
+        ov[i] = Obase[y * orow + xl];
+      }
+#pragma unroll
+      for (int i = 0; i < EB; ++i) {
+        const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+        const float2 psi1 = slab[ColA::at(xl, y)];
+        const float2 d = csub(psi1, cmul(pv[i], ov[i]));
+        const float2 uo = cmulc(pv[i], d);  // conj(P) Delta
+        const float2 up = cmulc(ov[i], d);  // conj(O_old) Delta
+        Obase[y * orow + xl] = make_float2(fmaf(ao, uo.x, ov[i].x), fmaf(ao, uo.y, ov[i].y));
+        part[y * N + xl] = cscale(up, bp);
+      }
     }
   } else if (ok) {
     // mini-batch: patches of a batch may overlap; the object moves once per
@@ -261,6 +334,10 @@ __global__ void __launch_bounds__(NT, (NT <= 512 ? 2 : 1)) epie_fused_kernel(Gro
     // the copy never arrived: give it one more bounded wait before exiting
     mbar_wait_bounded(bar, 0, 100000000ull);
   }
+#ifdef EPIE_PHASE_CLOCKS
+  __syncthreads();
+  EPIE_PHASE(13);
+#endif
 }
 
 template <int N, int CL, int NT, typename IT>

@@ -5,6 +5,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// CTAs per frame (thread-block cluster size) of the fused kernel per frame
+// side; every CTA holds N*N/CTAS complex values, 16 per thread.
+#ifndef EPIE_CTAS_64
+#define EPIE_CTAS_64 1
+#endif
+#ifndef EPIE_CTAS_128
+#define EPIE_CTAS_128 2
+#endif
+#ifndef EPIE_CTAS_256
+#define EPIE_CTAS_256 8
+#endif
+#ifndef EPIE_CTAS_512
+#define EPIE_CTAS_512 16
+#endif
+
 namespace epie {
 
 // Arguments of one group launch of the fused ePIE kernel (and of the plain
