@@ -27,7 +27,8 @@
  * paper's engine shuffles per iteration):
  *   EPIE_SEQUENTIAL  one position at a time (classic ePIE);
  *   EPIE_COLOURED    positions are grouped into colour classes whose patches
- *                    do not overlap (greedy first-fit in append order); a
+ *                    do not overlap (greedy first-fit in append order,
+ *                    optionally with a cap on the class size); a
  *                    class runs in parallel from the probe at class start and
  *                    the probe moves by the mean of its members' updates;
  *                    with one member per class this is EPIE_SEQUENTIAL;
@@ -124,11 +125,13 @@ typedef struct {
   int32_t device;          /* CUDA device ordinal                              */
   void *stream;            /* cudaStream_t to run on, or NULL for an own stream */
   uint32_t flags;          /* EPIE_CHECKED | EPIE_PROBE_SUM                     */
+  int32_t class_cap;       /* EPIE_COLOURED: at most this many frames per colour
+                              class (first-fit skips full classes); 0 = no cap  */
 } epie_config;
 
 /* Fills *cfg with defaults: N 256, object 1024^2, capacity 1024, EPIE_U16,
  * EPIE_COLOURED, batch 64, EPIE_OMAX_PATCH, EPIE_PATH_FUSED, alpha = beta = 1,
- * seed 0, device 0, own stream, no flags. */
+ * seed 0, device 0, own stream, no flags, no class cap. */
 EPIE_API void epie_config_default(epie_config *cfg);
 
 /* Creates a handle and allocates every device buffer the configuration needs.

@@ -32,7 +32,8 @@
  *      object at group start (omax_global).  A zero maximum turns the
  *      corresponding update off (0/0 := 0).
  *   R5 Intensities below 0 after dark subtraction, and NaN, are clamped to 0.
- *   R6 Coloured sweep: greedy first-fit colour classes in append order;
+ *   R6 Coloured sweep: greedy first-fit colour classes in append order
+ *      (optionally capped in size: a full class is skipped);
  *      members of a class share the probe at class start; the probe moves
  *      by the mean (or sum) of the members' probe updates.
  *   R7 Mini-batch sweep: a batch of consecutive positions of the shuffled
@@ -406,22 +407,26 @@ void orc_order_sequential(uint64_t seed, int64_t sweep, int32_t n, int32_t *orde
 
 /* Greedy first-fit colouring in index (append) order: frames i and j
  * conflict iff |y_i - y_j| < N and |x_i - x_j| < N; each frame takes the
- * smallest class id that no earlier conflicting frame holds.  Returns the
- * number of classes. */
-int32_t orc_colour_greedy(const int32_t *pos, int32_t n, int32_t N, int32_t *colour) {
+ * smallest class id that no earlier conflicting frame holds and that holds
+ * fewer than `cap` frames (cap <= 0: no limit).  Returns the number of
+ * classes. */
+int32_t orc_colour_greedy(const int32_t *pos, int32_t n, int32_t N, int32_t cap, int32_t *colour) {
   int32_t ncls = 0;
   uint8_t *used = (uint8_t *)calloc((size_t)n + 1, 1);
+  int32_t *size = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
   for (int32_t i = 0; i < n; ++i) {
     memset(used, 0, (size_t)ncls + 1);
     for (int32_t j = 0; j < i; ++j)
       if (abs(pos[2 * i] - pos[2 * j]) < N && abs(pos[2 * i + 1] - pos[2 * j + 1]) < N)
         used[colour[j]] = 1;
     int32_t c = 0;
-    while (c < ncls && used[c]) ++c;
+    while (c < ncls && (used[c] || (cap > 0 && size[c] >= cap))) ++c;
     colour[i] = c;
+    size[c] += 1;
     if (c == ncls) ++ncls;
   }
   free(used);
+  free(size);
   return ncls;
 }
 

@@ -58,7 +58,7 @@ def lib():
             L.orc_splitmix64.argtypes = [vp]
             L.orc_splitmix64.restype = u64
             L.orc_order_sequential.argtypes = [u64, i64, i32, vp]
-            L.orc_colour_greedy.argtypes = [vp, i32, i32, vp]
+            L.orc_colour_greedy.argtypes = [vp, i32, i32, i32, vp]
             L.orc_colour_greedy.restype = i32
             L.orc_order_coloured.argtypes = [u64, i64, i32, vp, i32, vp, vp]
             L.orc_amp_loss_grad.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp, vp, i32,
@@ -191,10 +191,12 @@ def order_sequential(seed, sweep, n):
     return out
 
 
-def colour_greedy(pos, N):
+def colour_greedy(pos, N, cap=0):
+    """Greedy first-fit colour classes (R6), at most `cap` frames per class
+    when cap > 0."""
     pos = np.ascontiguousarray(pos, dtype=np.int32)
     col = np.empty(len(pos), np.int32)
-    ncls = lib().orc_colour_greedy(_p(pos), len(pos), N, _p(col))
+    ncls = lib().orc_colour_greedy(_p(pos), len(pos), N, int(cap), _p(col))
     return col, int(ncls)
 
 
@@ -216,13 +218,13 @@ SEQUENTIAL, COLOURED = 0, 1
 
 
 def run_sweeps(O, P, I_all, pos, n_sweeps, N, seed, mode=SEQUENTIAL, alpha=1.0, beta=1.0,
-               sweep_offset=0, omax_global=False, probe_mean=True):
+               sweep_offset=0, omax_global=False, probe_mean=True, class_cap=0):
     """n_sweeps sweeps over all given frames, in place on O and P.
     Returns the per-sweep error metric E_s (R8)."""
     n = len(pos)
     errs = []
     if mode == COLOURED:
-        colour, ncls = colour_greedy(pos, N)
+        colour, ncls = colour_greedy(pos, N, class_cap)
     for s in range(sweep_offset, sweep_offset + n_sweeps):
         if mode == SEQUENTIAL:
             order = order_sequential(seed, s, n)

@@ -12,6 +12,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -159,8 +160,8 @@ int check_handle(epie_t h) {
 }
 
 // greedy first-fit colour of a new frame; frames conflict iff their patches
-// overlap (|dy| < N and |dx| < N).  A uniform grid of N x N cells finds the
-// candidates.
+// overlap (|dy| < N and |dx| < N); classes holding class_cap frames are
+// skipped.  A uniform grid of N x N cells finds the candidates.
 void colour_append(epie_ctx *h, int32_t f) {
   const int N = h->cfg.N;
   const int y = h->pos_h[2 * f], x = h->pos_h[2 * f + 1];
@@ -176,7 +177,9 @@ void colour_append(epie_ctx *h, int32_t f) {
     }
   int32_t c = 0;
   const int32_t nc = static_cast<int32_t>(h->classes.size());
-  while (c < nc && h->stamp[c] == static_cast<uint32_t>(f) + 1u) ++c;
+  const size_t cap = h->cfg.class_cap > 0 ? static_cast<size_t>(h->cfg.class_cap) : SIZE_MAX;
+  while (c < nc && (h->stamp[c] == static_cast<uint32_t>(f) + 1u || h->classes[c].size() >= cap))
+    ++c;
   if (c == nc) {
     h->classes.emplace_back();
     h->stamp.push_back(0);
@@ -400,6 +403,7 @@ void epie_config_default(epie_config *c) {
   c->device = 0;
   c->stream = nullptr;
   c->flags = 0;
+  c->class_cap = 0;
 }
 
 const char *epie_error(epie_t h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -460,6 +464,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.path != EPIE_PATH_FUSED && c.path != EPIE_PATH_PLAIN) why = "bad path";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
   else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM)) why = "unknown flags";
+  else if (c.class_cap < 0) why = "class_cap must be >= 0";
   if (!why.empty()) {
     g_init_error = "epie_init: " + why;
     return EPIE_EINVAL;

@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ 
   __shared__ float4 acc_sh[8][32];
   __shared__ double sh[8];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  grid_dependency_wait();  // the partials of the preceding step kernel
+  grid_dependents_launch();
   float best = -1.f;
   float2 bv = make_float2(0.f, 0.f);
   for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
@@ -345,9 +347,16 @@ cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t
 cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, int N, float scale,
                                 unsigned long long *pmax2_next, cudaStream_t st) {
   const int K = N * N;
-  probe_reduce_kernel<<<grid_for(K, 64, 152 * 4), 256, 0, st>>>(P, part, n_members, K, scale,
-                                                                 pmax2_next);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(K, 64, 152 * 4), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, probe_reduce_kernel, P, part, n_members, K, scale, pmax2_next);
 }
 
 cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, cudaStream_t st) {

@@ -70,11 +70,10 @@ struct FusedCfg {
 
 template <int N>
 struct ModReplace {
-  const float *itile;  // HR x N intensities max(I - dark, 0) of this CTA's rows
-  float e, s;          // sum (|Psi| - sqrt I)^2, sum I (FP32 per thread)
+  const float *sqtile;  // HR x N values sqrt(max(I - dark, 0)) of this CTA's rows
+  float e;              // sum (|Psi| - sqrt I)^2 (FP32 per thread)
   __device__ __forceinline__ float2 operator()(int b, int kx, float2 v) {
-    const float I = itile[b * N + kx];
-    const float sq = sqrtf(I);
+    const float sq = sqtile[b * N + kx];
     const float a2 = v.x * v.x + v.y * v.y;
     constexpr float invK = 1.0f / (float(N) * float(N));
     float2 out;
@@ -90,7 +89,6 @@ struct ModReplace {
     }
     const float d = amp - sq;
     e = fmaf(d, d, e);
-    s += I;
     return out;
   }
 };
@@ -139,6 +137,10 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
                   l2_evict_first_policy());
   }
   for (int m = tid; m < N; m += NT) tw[m] = a.twiddle[m];
+  // everything above reads data written before the sweep; the object, probe,
+  // max|P|^2 and the partial buffers are written by the preceding kernels
+  grid_dependency_wait();
+  grid_dependents_launch();
   if (blockIdx.x == 0 && tid == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
 
   // ---------------------------------------------------------------- phase 1
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   // ---------------------------------------------------------------- phase 2
   bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
+  float isum_t = 0.f;  // sum I of this thread's tile elements
   {
     // intensity tile -> float max(I - dark, 0), in place: the raw tile sits
     // at the top of the float tile, so every raw value is read (and the dark
@@ -231,16 +234,20 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < EI; ++i) itile[tid + i * NT] = fmaxf(iv[i], 0.f);
+    for (int i = 0; i < EI; ++i) {
+      const float I = fmaxf(iv[i], 0.f);
+      isum_t += I;
+      itile[tid + i * NT] = sqrtf(I);
+    }
     // the first row pass's barrier orders these writes before the modulus
   }
-  ModReplace<N> mod{itile, 0.f, 0.f};
+  ModReplace<N> mod{itile, 0.f};
   EPIE_PHASE(6);
   fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
   EPIE_PHASE(7);
   {
     // FP32 within a warp, FP64 across warps, CTAs and frames
-    const float e = warp_sum_f(mod.e), s = warp_sum_f(mod.s);
+    const float e = warp_sum_f(mod.e), s = warp_sum_f(isum_t);
     if (lane == 0) {
       red[2 + warp] = static_cast<double>(e);
       red[2 + NW + warp] = static_cast<double>(s);
@@ -364,15 +371,20 @@ cudaError_t launch_fused_t(const GroupArgs &a, cudaStream_t st) {
   cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
   if (CL > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
   }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 

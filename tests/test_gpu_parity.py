@@ -167,6 +167,21 @@ def test_coloured_one_sweep(orc, N, ny, nx, step, path):
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
 
 
+def test_coloured_with_class_cap(orc):
+    """Capped first-fit colouring (at most 3 frames per class): same classes,
+    order and result as the oracle's capped colouring."""
+    d = synth.small_scan(64, 5, 7, 33, seed=64)
+    st = textured_start(d)
+    O, P, e = sharp(orc, d, B.EPIE_COLOURED, st, class_cap=3)
+    with engine(d, B.EPIE_COLOURED, st, class_cap=3) as eng:
+        eng.append(d["frames"], d["pos"])
+        col, ncls = orc.colour_greedy(d["pos"], 64, cap=3)
+        assert np.array_equal(eng.colours(), col) and eng.n_classes == ncls
+        assert np.bincount(col).max() == 3
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+
+
 @pytest.mark.parametrize("N", [64, 256])
 def test_sequential_plain_path(orc, N):
     d = synth.small_scan(N, 3, 3, N // 3, seed=7)

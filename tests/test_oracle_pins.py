@@ -359,6 +359,15 @@ def test_colouring_valid_and_first_fit(orc):
         assert col[i] == min(set(range(ncls + 1)) - earlier)
     order, gs = orc.order_coloured(1, 3, col, ncls)
     assert sorted(order) == list(range(len(pos)))
+    # with a cap: classes stay valid, none exceeds the cap, and first-fit now
+    # skips full classes as well as conflicting ones
+    capc, ncap = orc.colour_greedy(pos, N, cap=5)
+    assert np.bincount(capc).max() <= 5 and ncap >= ncls
+    assert not np.any(conf & (capc[:, None] == capc[None, :]))
+    for i in range(len(pos)):
+        blocked = set(capc[:i][conf[i, :i]].tolist())
+        blocked |= {c for c in set(capc[:i].tolist()) if np.sum(capc[:i] == c) >= 5}
+        assert capc[i] == min(set(range(ncap + 1)) - blocked)
     for g in range(ncls):
         members = order[gs[g]:gs[g + 1]]
         assert len(set(col[members].tolist())) == 1
