@@ -81,14 +81,23 @@ def source_hash():
 
 def measured_traffic():
     """DRAM bytes per frame of the fused 256^2 kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "fused_256_traffic.json")
+    summary (key: value lines), if it was taken on the current kernel source
+    (else None)."""
+    p = os.path.join(ROOT, "profiles", "fused_256_traffic.txt")
+    rec = {}
     try:
         with open(p) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+    except OSError:
         return None
     if rec.get("source_hash") != source_hash():
+        return None
+    try:
+        rec["dram_bytes_per_frame"] = float(rec["dram_bytes_per_frame"])
+    except (KeyError, ValueError):
         return None
     return rec
 
@@ -156,6 +165,26 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
                 "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def replica_rate(units, seconds, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed divided by the slowest rank's time (max over ranks).  Works on
+    any initialised process group (gloo on CPU tensors, NCCL on CUDA ones);
+    without one it is units / seconds.  Returns (rate, max_seconds)."""
+    try:
+        import torch.distributed as dist
+        active = dist.is_available() and dist.is_initialized()
+    except ImportError:
+        active = False
+    if not active:
+        return units / seconds, seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
 
 
 # --------------------------------------------------------------------------- data
@@ -283,13 +312,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(device)
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- device-resident steps (value)
     for _ in range(args.warmup):
@@ -306,12 +328,13 @@ def run_ours(args):
             errs.append(float(step_device()[0]))
         ev1.record(stream)
         barrier()
-    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    dev_str = f"cuda:{device}"
+    value, elapsed_s = replica_rate(n * args.steps, ev0.elapsed_time(ev1) / 1e3, dev_str)
+    elapsed_ms = elapsed_s * 1e3
     launches = B.epie_launch_count(eng.h) - launches0
     k_launches, k_ms, k_frames = B.epie_kernel_timing(eng.h)
     B.epie_set_kernel_timing(eng.h, False)
     clocks = clk.summary()
-    value = n * args.steps * ws / (elapsed_ms / 1e3)
 
     # ---- end-to-end through the public API from pinned host memory
     for _ in range(max(1, args.warmup)):
@@ -321,8 +344,7 @@ def run_ours(args):
     for _ in range(args.steps):
         step_host()
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = n * args.steps * ws / e2e_s
+    e2e_value, _ = replica_rate(n * args.steps, time.perf_counter() - t0, dev_str)
     h2d = chunk_host.nbytes + chunk_pos.nbytes
     d2h = 8  # the sweep error
     eng.close()
