@@ -257,6 +257,46 @@ EPIE_API int epie_group_step_static(int32_t N, int32_t intensity_dtype, float *o
                                     const float *dark, float alpha, float beta,
                                     int32_t probe_mean, double *err_terms, void *stream);
 
+/* Differentiable reconstruction: the amplitude loss
+ *   L = sum_j sum_k ( |F(S_dj P . O_j)|(k) - sqrt(I_j(k)) )^2
+ * over positions j with patch O_j = O[y_j : y_j+N, x_j : x_j+N] and the probe
+ * shifted by the sub-pixel offset d_j = (dy, dx) as a Fourier shift
+ * S_d P = F^-1[ F P . exp(-2 pi i (ky dy + kx dx)/N) ] (frequencies in FFT
+ * order, k >= N/2 standing for k - N), together with its gradients.  ePIE
+ * (paper, Sec. "ePIE Implementation") projects onto the set this loss
+ * measures the distance to.  Gradients use dL/dRe + i dL/dIm (PyTorch's
+ * convention for real losses of complex tensors); where |Psi| = 0 the
+ * amplitude's gradient is taken as 0.  All pointers are device pointers
+ * except `loss` (host, may be NULL; when given the call waits for the result).
+ * The object and probe-spectrum gradients accumulate with float atomics, so
+ * their last bits may vary between runs; the loss and the position gradients
+ * are reduced in a fixed order.  N is 64, 128 or 256. */
+typedef struct {
+  int32_t N, intensity_dtype;  /* frame side; EPIE_U16 | EPIE_F16 | EPIE_F32      */
+  int32_t obj_h, obj_w, n;     /* object size, number of positions              */
+  const float *object;         /* obj_h*obj_w complex                           */
+  const float *probe;          /* N*N complex                                   */
+  const void *frames;          /* n*N*N intensities, FFT order (zero frequency
+                                  at [0,0], see epie_frames_to_fft_order)        */
+  const int32_t *pos;          /* n*(y, x) patch top-left, inside the object    */
+  const float *shift;          /* n*(dy, dx) sub-pixel offsets, or NULL (zero)   */
+  float *grad_object;          /* obj_h*obj_w complex, overwritten              */
+  float *grad_probe;           /* N*N complex, overwritten                      */
+  float *grad_shift;           /* n*2, overwritten, or NULL                     */
+  void *scratch;               /* device scratch of scratch_bytes               */
+  size_t scratch_bytes;        /* >= epie_amp_grad_scratch_bytes(N, n)           */
+  void *stream;                /* cudaStream_t                                  */
+} epie_amp_grad_args;
+EPIE_API size_t epie_amp_grad_scratch_bytes(int32_t N, int32_t n);
+EPIE_API int epie_amp_loss_grad(const epie_amp_grad_args *args, double *loss);
+
+/* Detector layout (zero frequency at the centre (N/2, N/2)) -> FFT order,
+ * on the device: dst[f][ky][kx] = src[f][(ky+N/2)%N][(kx+N/2)%N] for n frames
+ * of intensity_dtype elements (the re-layout epie_append_frames applies).
+ * src and dst must not overlap. */
+EPIE_API int epie_frames_to_fft_order(const void *src, void *dst, int32_t n, int32_t N,
+                                      int32_t intensity_dtype, void *stream);
+
 /* Message of the handle's last error (or of the last failed epie_init in
  * this thread when h is NULL).  Valid until the next call on the handle. */
 EPIE_API const char *epie_error(epie_t h);

@@ -35,6 +35,15 @@ class epie_config(C.Structure):
                 ("class_cap", C.c_int32)]
 
 
+class epie_amp_grad_args(C.Structure):
+    _fields_ = [("N", C.c_int32), ("intensity_dtype", C.c_int32), ("obj_h", C.c_int32),
+                ("obj_w", C.c_int32), ("n", C.c_int32), ("object", C.c_void_p),
+                ("probe", C.c_void_p), ("frames", C.c_void_p), ("pos", C.c_void_p),
+                ("shift", C.c_void_p), ("grad_object", C.c_void_p), ("grad_probe", C.c_void_p),
+                ("grad_shift", C.c_void_p), ("scratch", C.c_void_p),
+                ("scratch_bytes", C.c_size_t), ("stream", C.c_void_p)]
+
+
 class EpieError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -76,6 +85,10 @@ def lib():
                                          C.POINTER(i64)]
         L.epie_group_step_static.argtypes = [i32, i32, vp, i32, i32, vp, vp, i32, vp, vp, i32,
                                              vp, C.c_float, C.c_float, i32, vp, vp]
+        L.epie_amp_grad_scratch_bytes.argtypes = [i32, i32]
+        L.epie_amp_grad_scratch_bytes.restype = C.c_size_t
+        L.epie_amp_loss_grad.argtypes = [C.POINTER(epie_amp_grad_args), C.POINTER(C.c_double)]
+        L.epie_frames_to_fft_order.argtypes = [vp, vp, i32, i32, i32, vp]
         L.epie_error.argtypes = [H]
         L.epie_error.restype = C.c_char_p
         L.epie_destroy.argtypes = [H]
@@ -252,6 +265,27 @@ def epie_group_step_static(N, intensity_dtype, object_ptr, obj_h, obj_w, probe_p
     if rc != EPIE_OK:
         raise EpieError(rc, epie_error(None))
     return err
+
+
+def epie_frames_to_fft_order(src_ptr, dst_ptr, n, N, intensity_dtype=EPIE_U16, stream=None):
+    """Device re-layout of n DC-centred frames into FFT order (integer device
+    addresses)."""
+    rc = lib().epie_frames_to_fft_order(C.c_void_p(src_ptr), C.c_void_p(dst_ptr), n, N,
+                                        intensity_dtype, C.c_void_p(stream) if stream else None)
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
+
+
+def epie_amp_grad_scratch_bytes(N, n):
+    return int(lib().epie_amp_grad_scratch_bytes(N, n))
+
+
+def epie_amp_loss_grad(args: epie_amp_grad_args, want_loss=True):
+    loss = C.c_double(0.0)
+    rc = lib().epie_amp_loss_grad(C.byref(args), C.byref(loss) if want_loss else None)
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
+    return loss.value
 
 
 # --------------------------------------------------------------------------- convenience

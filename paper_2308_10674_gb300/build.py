@@ -16,7 +16,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # extra nvcc flags (e.g. -DEPIE_CTAS_256=4 to build another cluster shape)
 EXTRA = os.environ.get("EPIE_NVCC_FLAGS", "").split()
 SOURCES = ["epie_abi.cpp", "epie_dispatch.cu", "epie_aux.cu", "epie_fused_64.cu",
-           "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu"]
+           "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu",
+           "epie_adjoint.cu"]
 
 
 def nvcc() -> str:

@@ -853,6 +853,22 @@ int epie_last_timing(epie_t h, double *ms, int64_t *kernels) {
   return EPIE_OK;
 }
 
+int epie_frames_to_fft_order(const void *src, void *dst, int32_t n, int32_t N,
+                             int32_t intensity_dtype, void *stream) {
+  if (!(N == 64 || N == 128 || N == 256 || N == 512) || n < 0 || (n > 0 && (!src || !dst)) ||
+      intensity_dtype < EPIE_U16 || intensity_dtype > EPIE_F32) {
+    g_init_error = "epie_frames_to_fft_order: bad arguments";
+    return EPIE_EINVAL;
+  }
+  cudaError_t e = epie::launch_ingest(src, dst, n, N, static_cast<int>(esize_of(intensity_dtype)),
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    g_init_error = std::string("epie_frames_to_fft_order: ") + cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  return EPIE_OK;
+}
+
 int epie_launch_count(epie_t h, int64_t *total) {
   if (!h || !total) return EPIE_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
