@@ -103,6 +103,13 @@ typedef struct epie_ctx *epie_t;
 /* compute path */
 #define EPIE_PATH_FUSED 0    /* one fused kernel per group (default)            */
 #define EPIE_PATH_PLAIN 1    /* separate gather / FFT / modulus / IFFT / update */
+#define EPIE_PATH_GEMM 2     /* DFT as dense GEMMs on the tensor cores          */
+
+/* operand precision of EPIE_PATH_GEMM (fp32 accumulation in every case) */
+#define EPIE_GEMM_BF16 0     /* bf16 operands                                    */
+#define EPIE_GEMM_TF32 1     /* tf32 operands                                    */
+#define EPIE_GEMM_BF16X3 2   /* split bf16: hi*hi + hi*lo + lo*hi                */
+#define EPIE_GEMM_FP32EMU 3  /* fp32 emulated on bf16 tensor cores (9 products)  */
 
 /* flags */
 #define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
@@ -119,7 +126,7 @@ typedef struct {
   int32_t mode;            /* EPIE_SEQUENTIAL | EPIE_COLOURED | EPIE_MINIBATCH  */
   int32_t batch;           /* EPIE_MINIBATCH: positions per batch (>= 1)        */
   int32_t omax_mode;       /* EPIE_OMAX_PATCH | EPIE_OMAX_GLOBAL                */
-  int32_t path;            /* EPIE_PATH_FUSED | EPIE_PATH_PLAIN                 */
+  int32_t path;            /* EPIE_PATH_FUSED | EPIE_PATH_PLAIN | EPIE_PATH_GEMM */
   float alpha, beta;       /* update strengths; the paper uses 1 and 1          */
   uint64_t seed;           /* visiting-order seed                              */
   int32_t device;          /* CUDA device ordinal                              */
@@ -127,11 +134,12 @@ typedef struct {
   uint32_t flags;          /* EPIE_CHECKED | EPIE_PROBE_SUM                     */
   int32_t class_cap;       /* EPIE_COLOURED: at most this many frames per colour
                               class (first-fit skips full classes); 0 = no cap  */
+  int32_t gemm_precision;  /* EPIE_PATH_GEMM: EPIE_GEMM_*                        */
 } epie_config;
 
 /* Fills *cfg with defaults: N 256, object 1024^2, capacity 1024, EPIE_U16,
  * EPIE_COLOURED, batch 64, EPIE_OMAX_PATCH, EPIE_PATH_FUSED, alpha = beta = 1,
- * seed 0, device 0, own stream, no flags, no class cap. */
+ * seed 0, device 0, own stream, no flags, no class cap, EPIE_GEMM_BF16X3. */
 EPIE_API void epie_config_default(epie_config *cfg);
 
 /* Creates a handle and allocates every device buffer the configuration needs.

@@ -19,7 +19,8 @@ EPIE_ECUDA, EPIE_ETIMEOUT, EPIE_ENUMERIC, EPIE_ESTATE = -4, -5, -6, -7
 EPIE_U16, EPIE_F16, EPIE_F32 = 0, 1, 2
 EPIE_SEQUENTIAL, EPIE_COLOURED, EPIE_MINIBATCH = 0, 1, 2
 EPIE_OMAX_PATCH, EPIE_OMAX_GLOBAL = 0, 1
-EPIE_PATH_FUSED, EPIE_PATH_PLAIN = 0, 1
+EPIE_PATH_FUSED, EPIE_PATH_PLAIN, EPIE_PATH_GEMM = 0, 1, 2
+EPIE_GEMM_BF16, EPIE_GEMM_TF32, EPIE_GEMM_BF16X3, EPIE_GEMM_FP32EMU = 0, 1, 2, 3
 EPIE_CHECKED, EPIE_PROBE_SUM = 1, 2
 
 STATUS = {0: "EPIE_OK", -1: "EPIE_EINVAL", -2: "EPIE_ERANGE", -3: "EPIE_ECAPACITY",
@@ -32,7 +33,7 @@ class epie_config(C.Structure):
                 ("batch", C.c_int32), ("omax_mode", C.c_int32), ("path", C.c_int32),
                 ("alpha", C.c_float), ("beta", C.c_float), ("seed", C.c_uint64),
                 ("device", C.c_int32), ("stream", C.c_void_p), ("flags", C.c_uint32),
-                ("class_cap", C.c_int32)]
+                ("class_cap", C.c_int32), ("gemm_precision", C.c_int32)]
 
 
 class epie_amp_grad_args(C.Structure):
@@ -296,13 +297,14 @@ class Engine:
     def __init__(self, N, obj_h, obj_w, probe0, object0=None, capacity=1024,
                  intensity_dtype=EPIE_U16, mode=EPIE_COLOURED, batch=64,
                  omax_mode=EPIE_OMAX_PATCH, path=EPIE_PATH_FUSED, alpha=1.0, beta=1.0, seed=0,
-                 device=0, stream=None, flags=0, class_cap=0):
+                 device=0, stream=None, flags=0, class_cap=0, gemm_precision=EPIE_GEMM_BF16X3):
         cfg = epie_config_default()
         cfg.N, cfg.obj_h, cfg.obj_w, cfg.capacity = N, obj_h, obj_w, capacity
         cfg.intensity_dtype, cfg.mode, cfg.batch = intensity_dtype, mode, batch
         cfg.omax_mode, cfg.path, cfg.alpha, cfg.beta = omax_mode, path, alpha, beta
         cfg.seed, cfg.device, cfg.stream, cfg.flags = seed, device, stream, flags
         cfg.class_cap = class_cap
+        cfg.gemm_precision = gemm_precision
         self.cfg = cfg
         self.h = epie_init(cfg, probe0, object0)
 

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXTRA = os.environ.get("EPIE_NVCC_FLAGS", "").split()
 SOURCES = ["epie_abi.cpp", "epie_dispatch.cu", "epie_aux.cu", "epie_fused_64.cu",
            "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu",
-           "epie_adjoint.cu"]
+           "epie_adjoint.cu", "epie_gemm.cu"]
 
 
 def nvcc() -> str:
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     libdir = cuda_lib_dir()
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, f"-L{libdir}", "-lcufft",
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, f"-L{libdir}", "-lcufft", "-lcublas",
            "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -108,6 +108,8 @@ struct epie_ctx {
   int psi_cap = 0;
   double *omax_m = nullptr;
   std::map<int, cufftHandle> plans;
+  // tensor-core DFT path
+  epie::GemmPath *gemm = nullptr;
   // mini-batch accumulators
   float2 *accO = nullptr;
   int *cnt = nullptr;
@@ -301,6 +303,10 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, int64_t *ker
   if (h->cfg.path == EPIE_PATH_FUSED) {
     CK(epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st));
     *kernels += 1;
+  } else if (h->cfg.path == EPIE_PATH_GEMM) {
+    std::string why;
+    if ((rc = epie::gemm_path_group(h->gemm, a, h->cfg.intensity_dtype, h->st, &why, kernels)))
+      return h->fail(rc, "GEMM path: %s", why.c_str());
   } else {
     cufftHandle plan;
     if ((rc = get_plan(h, n_members, &plan))) return rc;
@@ -404,6 +410,7 @@ void epie_config_default(epie_config *c) {
   c->stream = nullptr;
   c->flags = 0;
   c->class_cap = 0;
+  c->gemm_precision = EPIE_GEMM_BF16X3;
 }
 
 const char *epie_error(epie_t h) { return h ? h->err.c_str() : g_init_error.c_str(); }
@@ -416,6 +423,7 @@ int epie_destroy(epie_t h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->up) cudaStreamSynchronize(h->up);
     for (auto &kv : h->plans) cufftDestroy(kv.second);
+    epie::gemm_path_destroy(h->gemm);
     void *dev[] = {h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
                    h->probe_part, h->err_part, h->isum_part, h->pmax2, h->omax_glob,
                    h->omax_tmp, h->err_out, h->flag_d, h->O_keep, h->P_keep, h->psi,
@@ -461,7 +469,9 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.mode < EPIE_SEQUENTIAL || c.mode > EPIE_MINIBATCH) why = "bad mode";
   else if (c.mode == EPIE_MINIBATCH && c.batch < 1) why = "batch must be >= 1";
   else if (c.omax_mode != EPIE_OMAX_PATCH && c.omax_mode != EPIE_OMAX_GLOBAL) why = "bad omax_mode";
-  else if (c.path != EPIE_PATH_FUSED && c.path != EPIE_PATH_PLAIN) why = "bad path";
+  else if (c.path < EPIE_PATH_FUSED || c.path > EPIE_PATH_GEMM) why = "bad path";
+  else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_FP32EMU)
+    why = "bad gemm_precision";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
   else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM)) why = "unknown flags";
   else if (c.class_cap < 0) why = "class_cap must be >= 0";
@@ -486,7 +496,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   // partial error slots per frame: one per CTA of the fused kernel, one per
   // block of the plain path's modulus kernel; every slot is written each sweep
   h->err_stride = c.path == EPIE_PATH_FUSED ? epie::fused_ctas_per_frame(c.N)
-                                            : epie::plain_err_stride(c.N);
+                                            : epie::plain_err_stride(c.N);  // plain and GEMM
   h->cell_rows = (c.obj_h + c.N - 1) / c.N;
   h->cell_cols = (c.obj_w + c.N - 1) / c.N;
   h->cells.resize(static_cast<size_t>(h->cell_rows) * h->cell_cols);
@@ -570,6 +580,14 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
     IK(cudaMemcpy(h->O, object0, sizeof(float2) * h->HW, cudaMemcpyHostToDevice));
   } else {
     IK(epie::launch_fill(h->O, h->HW, make_float2(1.f, 0.f), h->st));
+  }
+  if (c.path == EPIE_PATH_GEMM) {
+    std::string why;
+    h->gemm = epie::gemm_path_create(c.N, c.gemm_precision, h->st, &why);
+    if (!h->gemm) {
+      h->err = "epie_init: " + why;
+      return init_fail(h, EPIE_ECUDA);
+    }
   }
   if (recompute_pmax(h) != EPIE_OK) return init_fail(h, EPIE_ECUDA);
   IK(cudaStreamSynchronize(h->st));

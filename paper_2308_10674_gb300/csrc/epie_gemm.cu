@@ -1,0 +1,302 @@
+// epie_gemm.cu -- the ePIE step with the 2-D DFT done as dense GEMMs on the
+// tensor cores (precision study).
+//
+// The paper's engine projects with a DFT on 2^n frames (Sec. "ePIE
+// Implementation"); here the DFT of a group of G frames is four real GEMMs
+// per direction-pair instead of an FFT.  A row of interleaved complex values
+// (length N) times the real 2N x 2N matrix T with
+//   T[2k][2j] = Re F_kj, T[2k+1][2j] = -Im F_kj, T[2k][2j+1] = Im F_kj,
+//   T[2k+1][2j+1] = Re F_kj,       F_kj = exp(-+ 2 pi i k j / N)
+// is the row's DFT, so all G*N rows transform in one [G N x 2N] x [2N x 2N]
+// GEMM.  The column DFT is the same GEMM after a per-frame transpose:
+//   gather psi -> rows -> transpose -> rows (spectrum, transposed) ->
+//   modulus -> rows^-1 -> transpose -> rows^-1 -> update.
+// The GEMMs are plain library GEMMs (cuBLAS); gather, transposes, precision
+// splits, modulus and update are this engine's kernels.  Precisions:
+//   EPIE_GEMM_BF16    bf16 operands, fp32 accumulation (one GEMM)
+//   EPIE_GEMM_TF32    fp32 operands rounded to tf32 by the tensor cores
+//   EPIE_GEMM_BF16X3  x = x_hi + x_lo in bf16; A B ~ Ah Bh + Ah Bl + Al Bh
+//   EPIE_GEMM_FP32EMU cuBLAS' fp32 emulation on bf16 tensor cores
+// Twiddles are evaluated in double precision on the host (exact k j mod N).
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/epie.h"
+#include "epie_fft.cuh"
+#include "epie_internal.h"
+
+namespace epie {
+
+struct GemmPath {
+  int N = 0, precision = 0, cap = 0;
+  cublasHandle_t blas = nullptr;
+  float *Tf = nullptr, *Ti = nullptr;                       // fp32 forward / inverse, 2N x 2N
+  __nv_bfloat16 *Tf_hi = nullptr, *Tf_lo = nullptr, *Ti_hi = nullptr, *Ti_lo = nullptr;
+  float2 *psi = nullptr, *Y = nullptr;                      // cap * N * N complex each
+  __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;           // cap * N * 2N
+  double *omax = nullptr;                                   // cap
+};
+
+namespace {
+
+__global__ void split_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float v = x[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// out[b][j][i] = in[b][i][j] for G frames of N x N complex (32 x 32 tiles)
+__global__ void transpose_frames_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                        int N) {
+  __shared__ float2 t[32][33];
+  const size_t base = static_cast<size_t>(blockIdx.z) * N * N;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) t[r][threadIdx.x] = in[base + (by + r) * N + bx + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8)
+    out[base + (bx + r) * N + by + threadIdx.x] = t[threadIdx.x][r];
+}
+
+// modulus replacement on the transposed spectrum Xt[b][kx][ky] (1/N^2 folded
+// in), error partials per 1024-element block like the plain path
+template <typename IT>
+__global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt) {
+  __shared__ double se[8], ss[8];
+  const int m = blockIdx.y, K = N * N;
+  const int f = a.members[m];
+  const IT *I = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * K;
+  const float invK = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
+  float e = 0.f, s = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int t = blockIdx.x * 1024 + r * 256 + threadIdx.x;  // index in Xt: kx * N + ky
+    const int kx = t / N, ky = t % N;
+    float In = ival(I[ky * N + kx]);
+    if (a.dark) In -= a.dark[ky * N + kx];
+    In = fmaxf(In, 0.f);
+    const float sq = sqrtf(In);
+    float2 v = Xt[static_cast<size_t>(m) * K + t];
+    const float a2 = v.x * v.x + v.y * v.y;
+    float amp;
+    if (a2 > 0.f) {
+      const float ia = rsqrtf(a2);
+      amp = a2 * ia;
+      v = cscale(v, sq * ia * invK);
+    } else {
+      amp = 0.f;
+      v = make_float2(sq * invK, 0.f);
+    }
+    Xt[static_cast<size_t>(m) * K + t] = v;
+    const float d = amp - sq;
+    e = fmaf(d, d, e);
+    s += In;
+  }
+  const float we = warp_sum_f(e), ws = warp_sum_f(s);
+  if ((threadIdx.x & 31) == 0) {
+    se[threadIdx.x >> 5] = we;
+    ss[threadIdx.x >> 5] = ws;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double te = 0.0, ts = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      te += se[w];
+      ts += ss[w];
+    }
+    a.err_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = te;
+    a.isum_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = ts;
+  }
+}
+
+int grid_for(long long n, int nt, int cap) {
+  long long g = (n + nt - 1) / nt;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+cudaError_t split(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long n,
+                  cudaStream_t st) {
+  split_bf16_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(x, hi, lo, n);
+  return cudaGetLastError();
+}
+
+// dst (rows x 2N fp32) = src (rows x 2N) * T, T the 2N x 2N twiddle matrix
+int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool inverse,
+             cudaStream_t st, std::string *err) {
+  const int n2 = 2 * g->N;
+  const float one = 1.f, zero = 0.f;
+  const int M = static_cast<int>(rows);
+  cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
+  const float *srcf = reinterpret_cast<const float *>(src);
+  float *dstf = reinterpret_cast<float *>(dst);
+  if (g->precision == EPIE_GEMM_TF32 || g->precision == EPIE_GEMM_FP32EMU) {
+    const cublasComputeType_t ct = g->precision == EPIE_GEMM_TF32
+                                       ? CUBLAS_COMPUTE_32F_FAST_TF32
+                                       : CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+    s = cublasGemmEx(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, M, n2, &one, inverse ? g->Ti : g->Tf,
+                     CUDA_R_32F, n2, srcf, CUDA_R_32F, n2, &zero, dstf, CUDA_R_32F, n2, ct,
+                     CUBLAS_GEMM_DEFAULT);
+  } else {
+    const bool x3 = g->precision == EPIE_GEMM_BF16X3;
+    cudaError_t e = split(srcf, g->D_hi, x3 ? g->D_lo : nullptr, rows * n2, st);
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return EPIE_ECUDA;
+    }
+    const __nv_bfloat16 *Th = inverse ? g->Ti_hi : g->Tf_hi, *Tl = inverse ? g->Ti_lo : g->Tf_lo;
+    s = cublasGemmEx(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, M, n2, &one, Th, CUDA_R_16BF, n2,
+                     g->D_hi, CUDA_R_16BF, n2, &zero, dstf, CUDA_R_32F, n2, CUBLAS_COMPUTE_32F,
+                     CUBLAS_GEMM_DEFAULT);
+    if (x3 && s == CUBLAS_STATUS_SUCCESS)
+      s = cublasGemmEx(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, M, n2, &one, Th, CUDA_R_16BF, n2,
+                       g->D_lo, CUDA_R_16BF, n2, &one, dstf, CUDA_R_32F, n2, CUBLAS_COMPUTE_32F,
+                       CUBLAS_GEMM_DEFAULT);
+    if (x3 && s == CUBLAS_STATUS_SUCCESS)
+      s = cublasGemmEx(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, M, n2, &one, Tl, CUDA_R_16BF, n2,
+                       g->D_hi, CUDA_R_16BF, n2, &one, dstf, CUDA_R_32F, n2, CUBLAS_COMPUTE_32F,
+                       CUBLAS_GEMM_DEFAULT);
+  }
+  if (s != CUBLAS_STATUS_SUCCESS) {
+    *err = "cublasGemmEx failed (status " + std::to_string(static_cast<int>(s)) + ")";
+    return EPIE_ECUDA;
+  }
+  return EPIE_OK;
+}
+
+int transpose(GemmPath *g, const float2 *src, float2 *dst, int frames, cudaStream_t st,
+              std::string *err) {
+  dim3 grid(g->N / 32, g->N / 32, frames), block(32, 8);
+  transpose_frames_kernel<<<grid, block, 0, st>>>(src, dst, g->N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  return EPIE_OK;
+}
+
+}  // namespace
+
+void gemm_path_destroy(GemmPath *g) {
+  if (!g) return;
+  if (g->blas) cublasDestroy(g->blas);
+  void *ptrs[] = {g->Tf, g->Ti, g->Tf_hi, g->Tf_lo, g->Ti_hi, g->Ti_lo,
+                  g->psi, g->Y, g->D_hi, g->D_lo, g->omax};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete g;
+}
+
+GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *err) {
+  GemmPath *g = new GemmPath;
+  g->N = N;
+  g->precision = precision;
+  if (cublasCreate(&g->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(g->blas, st) != CUBLAS_STATUS_SUCCESS) {
+    *err = "cuBLAS initialisation failed";
+    gemm_path_destroy(g);
+    return nullptr;
+  }
+  const int n2 = 2 * N;
+  std::vector<float> Tf(static_cast<size_t>(n2) * n2), Ti(Tf.size());
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j) {
+      const long m = (static_cast<long>(k) * j) % N;
+      const double ang = -2.0 * 3.14159265358979323846 * static_cast<double>(m) / N;
+      const float c = static_cast<float>(std::cos(ang)), s = static_cast<float>(std::sin(ang));
+      // forward: F = c + i s; inverse (unnormalised): conj(F)
+      Tf[(2 * k) * n2 + 2 * j] = c;      Tf[(2 * k + 1) * n2 + 2 * j] = -s;
+      Tf[(2 * k) * n2 + 2 * j + 1] = s;  Tf[(2 * k + 1) * n2 + 2 * j + 1] = c;
+      Ti[(2 * k) * n2 + 2 * j] = c;      Ti[(2 * k + 1) * n2 + 2 * j] = s;
+      Ti[(2 * k) * n2 + 2 * j + 1] = -s; Ti[(2 * k + 1) * n2 + 2 * j + 1] = c;
+    }
+  const size_t tb = sizeof(float) * Tf.size(), hb = sizeof(__nv_bfloat16) * Tf.size();
+  bool ok = cudaMalloc(&g->Tf, tb) == cudaSuccess && cudaMalloc(&g->Ti, tb) == cudaSuccess &&
+            cudaMalloc(&g->Tf_hi, hb) == cudaSuccess && cudaMalloc(&g->Tf_lo, hb) == cudaSuccess &&
+            cudaMalloc(&g->Ti_hi, hb) == cudaSuccess && cudaMalloc(&g->Ti_lo, hb) == cudaSuccess;
+  ok = ok && cudaMemcpy(g->Tf, Tf.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(g->Ti, Ti.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && split(g->Tf, g->Tf_hi, g->Tf_lo, static_cast<long long>(Tf.size()), st) == cudaSuccess &&
+       split(g->Ti, g->Ti_hi, g->Ti_lo, static_cast<long long>(Ti.size()), st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    *err = "GEMM path: twiddle matrices could not be set up";
+    gemm_path_destroy(g);
+    return nullptr;
+  }
+  return g;
+}
+
+int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
+  if (members <= g->cap) return EPIE_OK;
+  const int cap = members > 2 * g->cap ? members : 2 * g->cap;
+  void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  g->psi = g->Y = nullptr;
+  g->D_hi = g->D_lo = nullptr;
+  g->omax = nullptr;
+  g->cap = 0;
+  const size_t K = static_cast<size_t>(g->N) * g->N;
+  bool ok = cudaMalloc(&g->psi, sizeof(float2) * K * cap) == cudaSuccess &&
+            cudaMalloc(&g->Y, sizeof(float2) * K * cap) == cudaSuccess &&
+            cudaMalloc(&g->omax, sizeof(double) * cap) == cudaSuccess;
+  if (ok && (g->precision == EPIE_GEMM_BF16 || g->precision == EPIE_GEMM_BF16X3)) {
+    ok = cudaMalloc(&g->D_hi, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
+    if (ok && g->precision == EPIE_GEMM_BF16X3)
+      ok = cudaMalloc(&g->D_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
+  }
+  if (!ok) {
+    *err = "GEMM path: out of device memory for a group of " + std::to_string(cap);
+    return EPIE_ECUDA;
+  }
+  g->cap = cap;
+  return EPIE_OK;
+}
+
+int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
+                    std::string *err, int64_t *kernels) {
+  const int N = g->N, G = a.n_members;
+  int rc = gemm_path_reserve(g, G, err);
+  if (rc) return rc;
+  const long long rows = static_cast<long long>(G) * N;
+  cudaError_t e = launch_plain_gather(a, N, g->psi, g->omax, st);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, st, err))) return rc;   // along x
+  if ((rc = transpose(g, g->Y, g->psi, G, st, err))) return rc;
+  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, st, err))) return rc;   // along y
+  dim3 grid(N * N / 1024, G);
+  if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, g->Y);
+  else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, g->Y);
+  else tmodulus_kernel<float><<<grid, 256, 0, st>>>(a, N, g->Y);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, st, err))) return rc;    // along y
+  if ((rc = transpose(g, g->psi, g->Y, G, st, err))) return rc;
+  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, st, err))) return rc;    // along x
+  e = a.accO ? launch_mb_accumulate(a, N, g->psi, g->omax, a.accO, a.cnt, st)
+             : launch_plain_update(a, N, g->psi, g->omax, st);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  const bool split_launch = g->precision == EPIE_GEMM_BF16 || g->precision == EPIE_GEMM_BF16X3;
+  *kernels += 5 + (split_launch ? 4 : 0);  // gather, 2 transposes, modulus, update (+ splits)
+  return EPIE_OK;
+}
+
+}  // namespace epie

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 // CTAs per frame (thread-block cluster size) of the fused kernel per frame
 // side; every CTA holds N*N/CTAS complex values, 16 per thread.
 #ifndef EPIE_CTAS_64
@@ -90,5 +92,12 @@ cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
                                  const double *omax2, float2 *accO, int *cnt, cudaStream_t st);
 cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
                             cudaStream_t st);
+
+// tensor-core DFT path (epie_gemm.cu)
+struct GemmPath;
+GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *err);
+void gemm_path_destroy(GemmPath *g);
+int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st, std::string *err,
+                    int64_t *kernels);
 
 }  // namespace epie

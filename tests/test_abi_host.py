@@ -49,7 +49,7 @@ int main(void) {{
   printf("%zu", sizeof(epie_config));
 #define F(m) printf(" %zu", offsetof(epie_config, m));
   F(N) F(obj_h) F(obj_w) F(capacity) F(intensity_dtype) F(mode) F(batch) F(omax_mode) F(path)
-  F(alpha) F(beta) F(seed) F(device) F(stream) F(flags) F(class_cap)
+  F(alpha) F(beta) F(seed) F(device) F(stream) F(flags) F(class_cap) F(gemm_precision)
   return 0;
 }}
 """)
@@ -73,7 +73,7 @@ def test_defaults(B):
     ("capacity", -1, "capacity"), ("intensity_dtype", 7, "intensity_dtype"),
     ("mode", 9, "mode"), ("omax_mode", 3, "omax_mode"), ("path", 4, "path"),
     ("flags", 1 << 8, "flags"), ("alpha", float("nan"), "finite"),
-    ("class_cap", -1, "class_cap"),
+    ("class_cap", -1, "class_cap"), ("gemm_precision", 9, "gemm_precision"),
 ])
 def test_bad_configuration_is_rejected_on_the_host(B, field, value, msg):
     c = B.epie_config_default()
