@@ -35,7 +35,8 @@
  *   EPIE_MINIBATCH   consecutive batches of `batch` positions share the
  *                    batch-start O and P; object updates are divided by the
  *                    per-pixel number of covering patches, probe updates
- *                    averaged.
+ *                    averaged (the overlapping object updates accumulate with
+ *                    float atomics, so results reproduce to rounding only).
  * The sweep error is E = sum_j sum_k (|Psi_j| - sqrt(I_j))^2 / sum_j sum_k I_j
  * (the paper defines none), accumulated in FP64.
  *
@@ -115,6 +116,10 @@ typedef struct epie_ctx *epie_t;
 #define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
                                 the sweep error is not finite                   */
 #define EPIE_PROBE_SUM 2u    /* coloured: probe moves by the sum, not the mean  */
+#define EPIE_GRAPH 4u        /* fused path: capture a sweep's launches in a CUDA
+                                graph once and replay it each sweep (the group
+                                table is uploaded per sweep; recaptured when the
+                                frame set or the dark field changes)           */
 
 typedef struct {
   int32_t N;               /* frame side: 64, 128, 256 or 512 (2^n frames, Sec.
@@ -180,6 +185,13 @@ EPIE_API int epie_truncate_frames(epie_t h, int32_t n_keep);
  * EPIE_CHECKED, O and P are then back at that sweep's start).  A sweep over
  * zero frames leaves the state unchanged and reports E = 0. */
 EPIE_API int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep);
+
+/* Several independent scans (handles, each with its own stream) sweep
+ * concurrently: every sweep of every handle is enqueued before any is waited
+ * for, so colour classes of different scans share the GPU.  err: k*n_sweeps
+ * doubles (handle-major) or NULL.  Returns the first failing handle's status
+ * (its message in epie_error(handle)); the other handles finish their sweeps. */
+EPIE_API int epie_iterate_many(epie_t *handles, int32_t k, int32_t n_sweeps, double *err);
 
 /* Object (obj_h*obj_w complex) and probe (N*N complex) export / import at a
  * sweep boundary (paper, Sec. "Discussion": import and export of object and

@@ -21,7 +21,7 @@ EPIE_SEQUENTIAL, EPIE_COLOURED, EPIE_MINIBATCH = 0, 1, 2
 EPIE_OMAX_PATCH, EPIE_OMAX_GLOBAL = 0, 1
 EPIE_PATH_FUSED, EPIE_PATH_PLAIN, EPIE_PATH_GEMM = 0, 1, 2
 EPIE_GEMM_BF16, EPIE_GEMM_TF32, EPIE_GEMM_BF16X3, EPIE_GEMM_FP32EMU = 0, 1, 2, 3
-EPIE_CHECKED, EPIE_PROBE_SUM = 1, 2
+EPIE_CHECKED, EPIE_PROBE_SUM, EPIE_GRAPH = 1, 2, 4
 
 STATUS = {0: "EPIE_OK", -1: "EPIE_EINVAL", -2: "EPIE_ERANGE", -3: "EPIE_ECAPACITY",
           -4: "EPIE_ECUDA", -5: "EPIE_ETIMEOUT", -6: "EPIE_ENUMERIC", -7: "EPIE_ESTATE"}
@@ -71,6 +71,7 @@ def lib():
         L.epie_append_frames_device.argtypes = [H, vp, vp, i32]
         L.epie_truncate_frames.argtypes = [H, i32]
         L.epie_iterate.argtypes = [H, i32, vp]
+        L.epie_iterate_many.argtypes = [vp, i32, i32, vp]
         for n in ("epie_get_object", "epie_get_probe", "epie_set_object", "epie_set_probe"):
             getattr(L, n).argtypes = [H, vp, sz]
         L.epie_num_frames.argtypes = [H, C.POINTER(i32)]
@@ -164,6 +165,19 @@ def epie_truncate_frames(h, n_keep):
 def epie_iterate(h, n_sweeps):
     err = np.zeros(max(n_sweeps, 0), np.float64)
     _check(h, lib().epie_iterate(h, n_sweeps, _p(err) if n_sweeps > 0 else None))
+    return err
+
+
+def epie_iterate_many(handles, n_sweeps):
+    """Concurrent sweeps of several handles; returns errors [len(handles), n_sweeps]."""
+    k = len(handles)
+    arr = (C.c_void_p * k)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    err = np.zeros((k, max(n_sweeps, 0)), np.float64)
+    rc = lib().epie_iterate_many(C.cast(arr, C.c_void_p), k, n_sweeps,
+                                 _p(err) if n_sweeps > 0 else None)
+    if rc != EPIE_OK:
+        msgs = "; ".join(epie_error(h) for h in handles if epie_error(h))
+        raise EpieError(rc, msgs or epie_error(None))
     return err
 
 

@@ -110,6 +110,15 @@ struct epie_ctx {
   std::map<int, cufftHandle> plans;
   // tensor-core DFT path
   epie::GemmPath *gemm = nullptr;
+  // graph replay of a sweep (EPIE_GRAPH)
+  int32_t *gstart_d = nullptr;          // device group table, capacity + 1
+  int32_t *order_h[2] = {nullptr, nullptr}, *gstart_h[2] = {nullptr, nullptr};  // pinned
+  cudaEvent_t ev_order[2] = {nullptr, nullptr};
+  int order_buf = 0;
+  double *err_sweep = nullptr;          // the graph's sweep error
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  long long gkey[6] = {-1, -1, -1, -1, -1, -1};
   // mini-batch accumulators
   float2 *accO = nullptr;
   int *cnt = nullptr;
@@ -348,6 +357,111 @@ int recompute_pmax(epie_ctx *h) {
   return EPIE_OK;
 }
 
+// Graph replay of a fused-path sweep: the launches read their group from
+// the device table, so one capture serves every sweep with the same number
+// of groups and the same largest group.
+int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
+                    const std::vector<int32_t> &gstart, int64_t *kernels) {
+  const int32_t n = h->n_frames;
+  const int ng = static_cast<int>(gstart.size()) - 1;
+  int maxg = 0;
+  for (int g = 0; g < ng; ++g) maxg = std::max(maxg, gstart[g + 1] - gstart[g]);
+  int rc = ensure_part(h, maxg);
+  if (rc) return rc;
+  // upload the table through a pinned buffer that the previous use released
+  const int b = h->order_buf;
+  h->order_buf ^= 1;
+  CK(cudaEventSynchronize(h->ev_order[b]));
+  std::copy(order.begin(), order.end(), h->order_h[b]);
+  std::copy(gstart.begin(), gstart.end(), h->gstart_h[b]);
+  CK(cudaMemcpyAsync(h->order_d, h->order_h[b], sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->gstart_d, h->gstart_h[b], sizeof(int32_t) * (ng + 1),
+                     cudaMemcpyHostToDevice, h->st));
+  CK(cudaEventRecord(h->ev_order[b], h->st));
+  if (h->pslot != 0) {  // the captured sweep starts from slot 0
+    CK(epie::launch_copy_u64(h->pmax2 + 1, h->pmax2, h->st));
+    h->pslot = 0;
+    *kernels += 1;
+  }
+  const long long key[6] = {n, ng, maxg, h->has_dark ? 1 : 0,
+                            static_cast<long long>(reinterpret_cast<uintptr_t>(h->probe_part)),
+                            h->cfg.omax_mode};
+  if (!h->gexec || !std::equal(key, key + 6, h->gkey)) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    {  // configure the kernel (shared-memory size, cluster shape) outside the capture
+      GroupArgs z{};
+      CK(epie::launch_fused(h->cfg.N, h->cfg.intensity_dtype, z, h->st));
+    }
+    const int N = h->cfg.N;
+    const bool mb = h->cfg.mode == EPIE_MINIBATCH;
+    const int mean = mb || (h->cfg.mode == EPIE_COLOURED && !(h->cfg.flags & EPIE_PROBE_SUM));
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    int p = 0;
+    cudaError_t ce = cudaSuccess;
+    for (int g = 0; g < ng && ce == cudaSuccess; ++g) {
+      GroupArgs a{};
+      a.O = h->O;
+      a.W = h->cfg.obj_w;
+      a.P = h->P;
+      a.frames = h->frames;
+      a.dark = h->has_dark ? h->dark_d : nullptr;
+      a.pos = h->pos_d;
+      a.members = h->order_d;
+      a.n_members = maxg;  // grid size; the table gives the group's own size
+      a.gstart = h->gstart_d;
+      a.group = g;
+      a.probe_part = h->probe_part;
+      a.err_part = h->err_part;
+      a.isum_part = h->isum_part;
+      a.err_stride = h->err_stride;
+      a.pmax2 = h->pmax2 + p;
+      a.pmax2_clear = h->pmax2 + (p ^ 1);
+      a.twiddle = h->twiddle;
+      a.alpha = h->cfg.alpha;
+      a.beta = h->cfg.beta;
+      a.err_flag = h->flag_d;
+      a.accO = mb ? h->accO : nullptr;
+      a.cnt = mb ? h->cnt : nullptr;
+      if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
+        ce = epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st);
+        a.omax2_global = h->omax_glob;
+      }
+      if (ce == cudaSuccess) ce = epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st);
+      if (ce == cudaSuccess && mb)
+        ce = epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st);
+      if (ce == cudaSuccess)
+        ce = epie::launch_probe_reduce_table(h->P, h->probe_part, h->gstart_d, g, mean, N,
+                                             h->pmax2 + (p ^ 1), h->st);
+      p ^= 1;
+    }
+    if (ce == cudaSuccess && p == 1) ce = epie::launch_copy_u64(h->pmax2 + 1, h->pmax2, h->st);
+    if (ce == cudaSuccess)
+      ce = epie::launch_error_reduce(h->err_part, h->isum_part, n, h->err_stride, h->err_sweep,
+                                     h->st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->st, &graph);
+    if (ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return h->cuda_fail(ce, "sweep capture");
+    }
+    if (ee != cudaSuccess) return h->cuda_fail(ee, "cudaStreamEndCapture");
+    h->graph = graph;
+    CK(cudaGraphInstantiate(&h->gexec, graph, 0));
+    std::copy(key, key + 6, h->gkey);
+  }
+  CK(cudaGraphLaunch(h->gexec, h->st));
+  CK(cudaMemcpyAsync(h->err_out + slot, h->err_sweep, sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->st));
+  const bool mb = h->cfg.mode == EPIE_MINIBATCH;
+  *kernels += static_cast<int64_t>(ng) * (2 + (mb ? 1 : 0) +
+                                          (h->cfg.omax_mode == EPIE_OMAX_GLOBAL ? 2 : 0)) +
+              1 + (ng % 2);
+  return EPIE_OK;
+}
+
 // one sweep over the frames present now; writes the sweep error to err_out[slot]
 int run_sweep(epie_ctx *h, int slot, int64_t *kernels) {
   const int32_t n = h->n_frames;
@@ -362,6 +476,8 @@ int run_sweep(epie_ctx *h, int slot, int64_t *kernels) {
   }
   std::vector<int32_t> order, gstart;
   make_order(h, h->sweep, n, order, gstart);
+  if ((h->cfg.flags & EPIE_GRAPH) && h->cfg.path == EPIE_PATH_FUSED && !h->ktime)
+    return run_sweep_graph(h, slot, order, gstart, kernels);
   CK(cudaMemcpyAsync(h->order_d, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st));
   const int ng = static_cast<int>(gstart.size()) - 1;
   for (int g = 0; g < ng; ++g) {
@@ -424,7 +540,14 @@ int epie_destroy(epie_t h) {
     if (h->up) cudaStreamSynchronize(h->up);
     for (auto &kv : h->plans) cufftDestroy(kv.second);
     epie::gemm_path_destroy(h->gemm);
-    void *dev[] = {h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (int b = 0; b < 2; ++b) {
+      if (h->order_h[b]) cudaFreeHost(h->order_h[b]);
+      if (h->gstart_h[b]) cudaFreeHost(h->gstart_h[b]);
+      if (h->ev_order[b]) cudaEventDestroy(h->ev_order[b]);
+    }
+    void *dev[] = {h->gstart_d, h->err_sweep, h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
                    h->probe_part, h->err_part, h->isum_part, h->pmax2, h->omax_glob,
                    h->omax_tmp, h->err_out, h->flag_d, h->O_keep, h->P_keep, h->psi,
                    h->omax_m, h->accO, h->cnt, h->stage_d};
@@ -473,7 +596,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_FP32EMU)
     why = "bad gemm_precision";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
-  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM)) why = "unknown flags";
+  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH)) why = "unknown flags";
   else if (c.class_cap < 0) why = "class_cap must be >= 0";
   if (!why.empty()) {
     g_init_error = "epie_init: " + why;
@@ -539,6 +662,14 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   IK(cudaMalloc(&h->err_out, sizeof(double) * 1024));
   IK(cudaMallocHost(&h->err_h, sizeof(double) * 1024));
   IK(cudaMalloc(&h->flag_d, sizeof(int)));
+  IK(cudaMalloc(&h->gstart_d, sizeof(int32_t) * (static_cast<size_t>(cap) + 1)));
+  IK(cudaMalloc(&h->err_sweep, sizeof(double)));
+  for (int b = 0; b < 2; ++b) {
+    IK(cudaMallocHost(&h->order_h[b], sizeof(int32_t) * static_cast<size_t>(cap)));
+    IK(cudaMallocHost(&h->gstart_h[b], sizeof(int32_t) * (static_cast<size_t>(cap) + 1)));
+    IK(cudaEventCreateWithFlags(&h->ev_order[b], cudaEventDisableTiming));
+    IK(cudaEventRecord(h->ev_order[b], h->st));
+  }
   IK(cudaMemsetAsync(h->flag_d, 0, sizeof(int), h->st));
   IK(cudaMemsetAsync(h->pmax2, 0, sizeof(unsigned long long) * 2, h->st));
   if (c.flags & EPIE_CHECKED) {
@@ -705,6 +836,75 @@ int epie_truncate_frames(epie_t h, int32_t n_keep) {
   h->colour.resize(n_keep);
   h->n_frames = n_keep;
   return EPIE_OK;
+}
+
+// Reads the errors of sweeps [s0, s0 + cnt) of this call from slots [first,
+// first + cnt), checks the device status word and non-finite errors (with
+// EPIE_CHECKED restoring the sweep start).  Call with h->mu held.
+static int fetch_errors(epie_t h, int first, int cnt, int32_t s0, double *err_per_sweep) {
+  CK(cudaMemcpyAsync(h->err_h + first, h->err_out + first, sizeof(double) * cnt,
+                     cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  int flag = 0;
+  CK(cudaMemcpy(&flag, h->flag_d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return h->fail(EPIE_ETIMEOUT, "a bounded device wait expired (flag %d)", flag);
+  for (int i = 0; i < cnt; ++i) {
+    const double e = h->err_h[first + i];
+    if (err_per_sweep) err_per_sweep[s0 + i] = e;
+    if (!std::isfinite(e))
+      return h->fail(EPIE_ENUMERIC, "sweep %lld: error metric is not finite",
+                     static_cast<long long>(h->sweep - cnt + i + 1));
+  }
+  return EPIE_OK;
+}
+
+int epie_iterate_many(epie_t *hs, int32_t k, int32_t n_sweeps, double *err) {
+  if (!hs || k < 0 || n_sweeps < 0) {
+    g_init_error = "epie_iterate_many: bad arguments";
+    return EPIE_EINVAL;
+  }
+  for (int32_t i = 0; i < k; ++i) {
+    int rc = check_handle(hs[i]);
+    if (rc) return rc;
+    if (hs[i]->cfg.flags & EPIE_CHECKED)
+      return hs[i]->fail(EPIE_EINVAL, "epie_iterate_many: EPIE_CHECKED handles need epie_iterate");
+    for (int32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return hs[i]->fail(EPIE_EINVAL, "epie_iterate_many: handle repeated");
+  }
+  int first_rc = EPIE_OK;
+  std::vector<int> failed(k, 0);
+  for (int32_t c0 = 0; c0 < n_sweeps; c0 += 1024) {
+    const int32_t cn = std::min<int32_t>(1024, n_sweeps - c0);
+    for (int32_t s = 0; s < cn; ++s)
+      for (int32_t i = 0; i < k; ++i) {
+        if (failed[i]) continue;
+        epie_t h = hs[i];
+        std::lock_guard<std::mutex> lk(h->mu);
+        int64_t kern = 0;
+        int rc = cudaSetDevice(h->cfg.device) == cudaSuccess ? EPIE_OK
+                                                             : h->fail(EPIE_ECUDA, "cudaSetDevice");
+        if (!rc) rc = run_sweep(h, s, &kern);
+        if (!rc) {
+          h->sweep += 1;
+          h->launches_total += kern;
+        }
+        if (rc) {
+          failed[i] = 1;
+          if (!first_rc) first_rc = rc;
+        }
+      }
+    for (int32_t i = 0; i < k; ++i) {
+      if (failed[i]) continue;
+      epie_t h = hs[i];
+      std::lock_guard<std::mutex> lk(h->mu);
+      int rc = fetch_errors(h, 0, cn, c0, err ? err + static_cast<size_t>(i) * n_sweeps : nullptr);
+      if (rc) {
+        failed[i] = 1;
+        if (!first_rc) first_rc = rc;
+      }
+    }
+  }
+  return first_rc;
 }
 
 int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep) {

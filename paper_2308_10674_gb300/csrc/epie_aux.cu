@@ -65,10 +65,16 @@ __global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restr
 __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ P,
                                                           const float2 *__restrict__ part,
                                                           int n_members, int K, float scale,
-                                                          unsigned long long *pmax2_next) {
+                                                          unsigned long long *pmax2_next,
+                                                          const int32_t *gstart, int group,
+                                                          int mean) {
   __shared__ float4 acc_sh[8][32];
   __shared__ double sh[8];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (gstart) {  // group size from the device table
+    n_members = gstart[group + 1] - gstart[group];
+    scale = mean ? 1.0f / static_cast<float>(n_members) : 1.0f;
+  }
   grid_dependency_wait();  // the partials of the preceding step kernel
   grid_dependents_launch();
   float best = -1.f;
@@ -356,7 +362,37 @@ cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, in
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, probe_reduce_kernel, P, part, n_members, K, scale, pmax2_next);
+  return cudaLaunchKernelEx(&cfg, probe_reduce_kernel, P, part, n_members, K, scale, pmax2_next,
+                            static_cast<const int32_t *>(nullptr), 0, 0);
+}
+
+cudaError_t launch_probe_reduce_table(float2 *P, const float2 *part, const int32_t *gstart,
+                                      int group, int mean, int N, unsigned long long *pmax2_next,
+                                      cudaStream_t st) {
+  const int K = N * N;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(K, 64, 152 * 4), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, probe_reduce_kernel, P, part, 0, K, 1.0f, pmax2_next, gstart,
+                            group, mean);
+}
+
+namespace {
+__global__ void copy_u64_kernel(const unsigned long long *src, unsigned long long *dst) {
+  *dst = *src;
+}
+}  // namespace
+
+cudaError_t launch_copy_u64(const unsigned long long *src, unsigned long long *dst,
+                            cudaStream_t st) {
+  copy_u64_kernel<<<1, 1, 0, st>>>(src, dst);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, cudaStream_t st) {

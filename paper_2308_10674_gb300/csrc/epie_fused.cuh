@@ -117,9 +117,17 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   EPIE_PHASE(0);
   const int member = blockIdx.x / CL;
+  const int32_t *members = a.members;
+  if (a.gstart) {
+    // device group table: a whole cluster past the group's size exits here,
+    // before any barrier or copy
+    const int g0 = a.gstart[a.group];
+    if (member >= a.gstart[a.group + 1] - g0) return;
+    members += g0;
+  }
   int crank = 0;
   if constexpr (CL > 1) crank = static_cast<int>(cg::this_cluster().block_rank());
-  const int f = a.members[member];
+  const int f = members[member];
   const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
   const IT *frame = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * N * N;
 

@@ -47,6 +47,11 @@ struct GroupArgs {
   int *err_flag;              // device status word (bounded waits)
   float2 *accO;               // mini-batch: object-update accumulator (H x W) or nullptr
   int *cnt;                   // mini-batch: per-pixel count of covering patches
+  // device group table (graph replay): when gstart is set, this launch runs
+  // group `group` with members members[gstart[group] .. gstart[group+1]) and
+  // the grid is sized for the largest group; surplus clusters exit at once
+  const int32_t *gstart;
+  int group;
 };
 
 // error-flag bits written by kernels
@@ -63,6 +68,14 @@ size_t fused_smem_bytes(int N, int itype);
 // max|P|^2 (double) into *pmax2_next (must be zero on entry)
 cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, int N, float scale,
                                 unsigned long long *pmax2_next, cudaStream_t st);
+// the same with the member count of group `group` read from the device table;
+// scale = 1/count when mean != 0, else 1
+cudaError_t launch_probe_reduce_table(float2 *P, const float2 *part, const int32_t *gstart,
+                                      int group, int mean, int N, unsigned long long *pmax2_next,
+                                      cudaStream_t st);
+// copy of 8 bytes on the device (graph-safe)
+cudaError_t launch_copy_u64(const unsigned long long *src, unsigned long long *dst,
+                            cudaStream_t st);
 // max|P|^2 of the probe into *pmax2 (zeroed by the kernel's caller)
 cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, cudaStream_t st);
 // max|O|^2 over the object into *out (double)
