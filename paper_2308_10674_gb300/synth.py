@@ -245,10 +245,14 @@ def _init_worker(O, P, D):
 def _frames_chunk(args):
     """Frames [a, b) of a scan; noise drawn from a substream keyed by the chunk
     index, so the result does not depend on how chunks are spread over workers."""
-    pos, seed, chunk, noise = args
+    pos, seed, chunk, noise, dtype = args
     lam = far_field_intensity(_W["O"], _W["P"], pos, dtype=np.complex64)
     if _W["D"] is not None:
         lam = lam + _W["D"][None].astype(np.float64)
+    if dtype == np.float16:
+        if noise:
+            lam = substream(seed, 1000 + chunk).poisson(lam).astype(np.float64)
+        return np.minimum(lam, 65504.0).astype(np.float16), float(np.mean(lam > 65504.0))
     if noise:
         return poisson_u16(lam, substream(seed, 1000 + chunk))
     return lam.astype(np.float32), 0.0
@@ -257,8 +261,32 @@ def _frames_chunk(args):
 LIVE_CHUNK = 250
 
 
+def scan(N, n, pattern="spiral", seed=0, photons=1e8, fwhm=None, noise=True, dark=False,
+         dtype=np.uint16, workers=1):
+    """Scan of n positions at frame side N on a "raster", "jittered" raster
+    (+-20% of the step, seeded) or Fermat "spiral", step 0.35 x the probe
+    FWHM (default FWHM 60 px x N/256), object and probe as in live_scan.
+    dtype float16 stores the (noisy or model) intensities as binary16,
+    clamped to 65504."""
+    fwhm = 60.0 * N / 256.0 if fwhm is None else fwhm
+    step = 0.35 * fwhm
+    rng_jit = substream(seed, 31)
+    if pattern == "spiral":
+        cen = fermat_spiral_centres(n, spiral_c_for_step(n, step))
+    else:
+        side = int(math.ceil(math.sqrt(n)))
+        iy, ix = np.divmod(np.arange(n), side)
+        cen = np.stack([iy * step, ix * step], axis=1).astype(np.float64)
+        if pattern == "jittered":
+            cen = cen + rng_jit.uniform(-0.2 * step, 0.2 * step, size=cen.shape)
+        elif pattern != "raster":
+            raise ValueError("pattern must be raster, jittered or spiral")
+    return live_scan(N=N, n=n, seed=seed, photons=photons, fwhm=fwhm, noise=noise, dark=dark,
+                     workers=workers, centres=cen, dtype=dtype)
+
+
 def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, noise=True,
-              dark=True, n_frames=None, workers=1):
+              dark=True, n_frames=None, workers=1, centres=None, dtype=np.uint16):
     """Beamline-like live workload: N x N uint16 frames on a Fermat spiral.
 
     geometry "A": step = 0.35 x probe FWHM (median nearest-neighbour distance),
@@ -272,19 +300,22 @@ def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, nois
     rng_obj, rng_dark = substream(seed, 11), substream(seed, 14)
     R = probe_radius_for_fwhm(N, fwhm)
     sig_ap = 3.0 * R / 20.0
-    if geometry == "A":
-        c = spiral_c_for_step(n, 0.35 * fwhm)
-    elif geometry == "B":
-        c = (1400 - N - 8) / 2.0 / math.sqrt(n)
-    else:
-        raise ValueError("geometry must be 'A' or 'B'")
-    tl, H, W = centres_to_topleft(fermat_spiral_centres(n, c), N, 4)
+    c = None
+    if centres is None:
+        if geometry == "A":
+            c = spiral_c_for_step(n, 0.35 * fwhm)
+        elif geometry == "B":
+            c = (1400 - N - 8) / 2.0 / math.sqrt(n)
+        else:
+            raise ValueError("geometry must be 'A' or 'B'")
+        centres = fermat_spiral_centres(n, c)
+    tl, H, W = centres_to_topleft(centres, N, 4)
     O_true = make_object(H, W, 4.0 * R / 20.0, rng_obj)
     m = n if n_frames is None else min(n, n_frames)
     pos = tl[:m]
     P_true = scale_probe_to_photons(O_true, make_probe(N, R, sig_ap), pos[: min(m, 500)], photons)
     D = dark_field(N, photons, rng_dark) if dark else None
-    jobs = [(pos[a:min(m, a + LIVE_CHUNK)], seed, a // LIVE_CHUNK, noise)
+    jobs = [(pos[a:min(m, a + LIVE_CHUNK)], seed, a // LIVE_CHUNK, noise, dtype)
             for a in range(0, m, LIVE_CHUNK)]
     O32, P32 = O_true.astype(np.complex64), P_true.astype(np.complex64)
     if workers > 1 and len(jobs) > 1:
@@ -297,7 +328,8 @@ def live_scan(N=256, n=10000, geometry="A", seed=0, photons=1e8, fwhm=60.0, nois
         _init_worker(O32, P32, D)
         parts = [_frames_chunk(j) for j in jobs]
     frames = (np.concatenate([p[0] for p in parts]) if parts else
-              np.empty((0, N, N), np.uint16 if noise else np.float32))
+              np.empty((0, N, N), dtype if dtype == np.float16 else
+                       (np.uint16 if noise else np.float32)))
     clamped = sum(p[1] * len(j[0]) for p, j in zip(parts, jobs)) / max(m, 1)
     return dict(N=N, H=H, W=W, pos=pos, frames=frames, O_true=O_true, P_true=P_true,
                 O0=np.ones((H, W), np.complex128), P0=initial_probe(N, R, sig_ap, photons),
