@@ -193,6 +193,13 @@ EPIE_API int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep);
  * (its message in epie_error(handle)); the other handles finish their sweeps. */
 EPIE_API int epie_iterate_many(epie_t *handles, int32_t k, int32_t n_sweeps, double *err);
 
+/* The paper's parallel scheme (Sec. "Simulating live and parallel
+ * processing": disjoint subsets iterated independently, then object and
+ * illumination averaged for synchronisation): replaces the object and probe
+ * of every handle by their mean over the k handles (FP32, summed in handle
+ * order).  All handles must share N, the object size and the device. */
+EPIE_API int epie_average_state(epie_t *handles, int32_t k);
+
 /* Object (obj_h*obj_w complex) and probe (N*N complex) export / import at a
  * sweep boundary (paper, Sec. "Discussion": import and export of object and
  * illumination through the API).  n_floats must equal 2*obj_h*obj_w or

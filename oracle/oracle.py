@@ -251,3 +251,22 @@ def amp_loss_grad(O, P, I_all, pos, shift=None):
     L = lib().orc_amp_loss_grad(_p(O), O.shape[0], O.shape[1], _p(P), P.shape[0], _p(I_all),
                                 _p(pos), _p(sh), n, _p(gO), _p(gP), _p(gd))
     return L, gO, gP, gd
+
+
+def run_parallel_average(O, P, I_all, pos, subsets, sweeps_per_round, rounds, N, seed,
+                         mode=SEQUENTIAL, **kw):
+    """The paper's parallel scheme (Sec. "Simulating live and parallel
+    processing"): every round, each disjoint subset q of positions runs
+    `sweeps_per_round` sweeps from the common (O, P) on its own copy (order
+    stream seed + q, sweep counter continuing across rounds), then O and P
+    become the mean of the copies (summed in subset order).  In place on O, P."""
+    for r in range(rounds):
+        Os, Ps = [], []
+        for q, idx in enumerate(subsets):
+            Oq, Pq = O.copy(), P.copy()
+            run_sweeps(Oq, Pq, I_all[idx], pos[idx], sweeps_per_round, N, seed + q, mode=mode,
+                       sweep_offset=r * sweeps_per_round, **kw)
+            Os.append(Oq)
+            Ps.append(Pq)
+        O[...] = sum(Os[1:], Os[0]) / len(Os)
+        P[...] = sum(Ps[1:], Ps[0]) / len(Ps)

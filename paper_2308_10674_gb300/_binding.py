@@ -72,6 +72,7 @@ def lib():
         L.epie_truncate_frames.argtypes = [H, i32]
         L.epie_iterate.argtypes = [H, i32, vp]
         L.epie_iterate_many.argtypes = [vp, i32, i32, vp]
+        L.epie_average_state.argtypes = [vp, i32]
         for n in ("epie_get_object", "epie_get_probe", "epie_set_object", "epie_set_probe"):
             getattr(L, n).argtypes = [H, vp, sz]
         L.epie_num_frames.argtypes = [H, C.POINTER(i32)]
@@ -179,6 +180,16 @@ def epie_iterate_many(handles, n_sweeps):
         msgs = "; ".join(epie_error(h) for h in handles if epie_error(h))
         raise EpieError(rc, msgs or epie_error(None))
     return err
+
+
+def epie_average_state(handles):
+    """Replace every handle's object and probe by their mean (paper's
+    parallel scheme)."""
+    k = len(handles)
+    arr = (C.c_void_p * k)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    rc = lib().epie_average_state(C.cast(arr, C.c_void_p), k)
+    if rc != EPIE_OK:
+        raise EpieError(rc, "; ".join(epie_error(h) for h in handles if epie_error(h)))
 
 
 def _get(h, fn, shape):

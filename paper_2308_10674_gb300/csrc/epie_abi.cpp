@@ -907,6 +907,55 @@ int epie_iterate_many(epie_t *hs, int32_t k, int32_t n_sweeps, double *err) {
   return first_rc;
 }
 
+int epie_average_state(epie_t *hs, int32_t k) {
+  if (!hs || k < 1) {
+    g_init_error = "epie_average_state: bad arguments";
+    return EPIE_EINVAL;
+  }
+  for (int32_t i = 0; i < k; ++i) {
+    int rc = check_handle(hs[i]);
+    if (rc) return rc;
+    const epie_config &a = hs[0]->cfg, &b = hs[i]->cfg;
+    if (a.N != b.N || a.obj_h != b.obj_h || a.obj_w != b.obj_w || a.device != b.device)
+      return hs[i]->fail(EPIE_EINVAL, "epie_average_state: handles differ in N, object or device");
+    for (int32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return hs[i]->fail(EPIE_EINVAL, "epie_average_state: handle repeated");
+  }
+  if (k == 1) return EPIE_OK;
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (int32_t i = 0; i < k; ++i) locks.emplace_back(hs[i]->mu);
+  epie_t h = hs[0];
+  CK(cudaSetDevice(h->cfg.device));
+  for (int32_t i = 0; i < k; ++i) CK(cudaStreamSynchronize(hs[i]->st));
+  // source pointer tables: objects, then probes
+  std::vector<const float2 *> tab(2 * static_cast<size_t>(k));
+  for (int32_t i = 0; i < k; ++i) {
+    tab[i] = hs[i]->O;
+    tab[k + i] = hs[i]->P;
+  }
+  const float2 **tab_d = nullptr;
+  CK(cudaMalloc(&tab_d, sizeof(float2 *) * tab.size()));
+  cudaError_t e = cudaMemcpy(tab_d, tab.data(), sizeof(float2 *) * tab.size(),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = epie::launch_average(tab_d, k, h->O, h->HW, h->st);
+  if (e == cudaSuccess) e = epie::launch_average(tab_d + k, k, h->P, h->K, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(tab_d);
+  if (e != cudaSuccess) return h->cuda_fail(e, "epie_average_state");
+  for (int32_t i = 1; i < k; ++i) {
+    CK(cudaMemcpyAsync(hs[i]->O, h->O, sizeof(float2) * h->HW, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(hs[i]->P, h->P, sizeof(float2) * h->K, cudaMemcpyDeviceToDevice, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  for (int32_t i = 0; i < k; ++i) {
+    int rc = recompute_pmax(hs[i]);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(hs[i]->st));
+  }
+  h->launches_total += 2;
+  return EPIE_OK;
+}
+
 int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep) {
   int rc = check_handle(h);
   if (rc) return rc;

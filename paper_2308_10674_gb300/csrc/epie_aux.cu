@@ -340,6 +340,25 @@ cudaError_t launch_ingest(const void *raw, void *dst, int n, int N, int esize, c
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void average_kernel(const float2 *const *__restrict__ src, int k, float2 *out,
+                               long long n) {
+  const float inv = 1.0f / static_cast<float>(k);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < k; ++q) acc = cadd(acc, src[q][i]);
+    out[i] = cscale(acc, inv);
+  }
+}
+}  // namespace
+
+cudaError_t launch_average(const float2 *const *src, int k, float2 *out, long long n,
+                           cudaStream_t st) {
+  average_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(src, k, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st) {
   fill_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(p, n, v);
   return cudaGetLastError();

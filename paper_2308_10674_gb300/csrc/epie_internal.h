@@ -86,6 +86,10 @@ cudaError_t launch_error_reduce(const double *err_part, const double *isum_part,
                                 int stride, double *out, cudaStream_t st);
 // live ingest: raw DC-centred frames -> device set in FFT order (ifftshift)
 cudaError_t launch_ingest(const void *raw, void *dst, int n, int N, int esize, cudaStream_t st);
+// out[i] = (1/k) sum_q src[q][i] (q in order) for n complex values; src is a
+// device array of k device pointers; out may be one of the sources
+cudaError_t launch_average(const float2 *const *src, int k, float2 *out, long long n,
+                           cudaStream_t st);
 // p[0..n) = v
 cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st);
 // dark field: DC-centred float -> FFT order
