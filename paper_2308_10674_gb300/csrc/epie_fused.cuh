@@ -96,7 +96,11 @@ struct ModReplace {
 // resident CTAs per SM the register budget is sized for
 template <int CL, int NT>
 constexpr int fused_min_blocks() {
+#ifdef EPIE_FUSED_MIN_BLOCKS
+  return EPIE_FUSED_MIN_BLOCKS;
+#else
   return CL == 1 ? 2 : (1024 / NT > 1 ? 1024 / NT : 1);
+#endif
 }
 
 template <int N, int CL, int NT, typename IT>
@@ -157,7 +161,20 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   const float2 *Pbase = a.P + crank * WC;
   float om = -1.f;
   float2 omv = make_float2(0.f, 0.f);
-  constexpr int EB = E >= 8 ? 8 : E;  // loads issued together (one latency per batch)
+#ifndef EPIE_LOAD_BATCH
+#define EPIE_LOAD_BATCH 8
+#endif
+  constexpr int EB = E >= EPIE_LOAD_BATCH ? EPIE_LOAD_BATCH : E;  // loads in flight together
+#ifndef EPIE_NO_OBJECT_L2_HINT
+  // the object is revisited by every later class: keep it in L2 ahead of the
+  // streamed frames and the probe partials
+  const uint64_t opol = l2_evict_last_policy();
+#define EPIE_LD_O(p) ld_l2hint((p), opol)
+#define EPIE_ST_O(p, v) st_l2hint((p), (v), opol)
+#else
+#define EPIE_LD_O(p) (*(p))
+#define EPIE_ST_O(p, v) (*(p) = (v))
+#endif
 #pragma unroll
   for (int i0 = 0; i0 < E; i0 += EB) {
     float2 pv[EB], ov[EB];
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     for (int i = 0; i < EB; ++i) {
       const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
       pv[i] = __ldg(Pbase + y * N + xl);
-      ov[i] = Obase[y * orow + xl];
+      ov[i] = EPIE_LD_O(Obase + y * orow + xl);
     }
 #pragma unroll
     for (int i = 0; i < EB; ++i) {
@@ -180,22 +197,32 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   fft_all<N, false, NT, WC, false, ColA>(slab, tw);
   EPIE_PHASE(2);
 
-  // max |O_old|^2 over the patch: FP32 comparisons pick the element, its
-  // square is formed in FP64 and the maximum over warps taken in FP64
+  // max |O_old|^2 over the patch: FP32 comparisons pick the element (lanes,
+  // then warps); its square is formed in FP64 for the cluster-wide maximum
   omv = warp_argmax_f(om, omv);
-  double omax = static_cast<double>(omv.x) * omv.x + static_cast<double>(omv.y) * omv.y;
-  if (lane == 0) red[2 + warp] = omax;
-  __syncthreads();
-  if (tid == 0) {
-    double m = red[2];
-    for (int w = 1; w < NW; ++w) m = fmax(m, red[2 + w]);
-    red[0] = m;
+  float *redf = reinterpret_cast<float *>(red + 2);  // per-warp candidates (re, im, |.|^2)
+  if (lane == 0) {
+    redf[3 * warp] = omv.x;
+    redf[3 * warp + 1] = omv.y;
+    redf[3 * warp + 2] = omv.x * omv.x + omv.y * omv.y;
   }
+  __syncthreads();
+  if (warp == 0) {
+    float2 c = make_float2(0.f, 0.f);
+    float q = -1.f;
+    if (lane < NW) {
+      c = make_float2(redf[3 * lane], redf[3 * lane + 1]);
+      q = redf[3 * lane + 2];
+    }
+    c = warp_argmax_f(q, c);
+    if (lane == 0) red[0] = static_cast<double>(c.x) * c.x + static_cast<double>(c.y) * c.y;
+  }
+  double omax = 0.0;
 
   if constexpr (CL > 1) {
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();  // column transforms and red[0] of every CTA visible
-  EPIE_PHASE(3);
+    EPIE_PHASE(3);
     constexpr int CH = HR * WC / 2;  // float4 per (peer, this CTA) block
     float4 t4[E / 2];
 #pragma unroll
@@ -204,9 +231,11 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(slab, q));
       t4[i] = src[crank * CH + off];
     }
-    double om_all = 0.0;
-    for (int q = 0; q < CL; ++q) om_all = fmax(om_all, *cluster.map_shared_rank(red, q));
-  EPIE_PHASE(4);
+    // one remote load per lane: lane q < CL fetches CTA q's patch maximum
+    double om_all = lane < CL ? *cluster.map_shared_rank(red, lane) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) om_all = fmax(om_all, __shfl_xor_sync(0xffffffffu, om_all, o));
+    EPIE_PHASE(4);
     cluster.sync();  // all remote reads done before the tile is overwritten
 #pragma unroll
     for (int i = 0; i < E / 2; ++i) {
@@ -217,7 +246,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     }
     omax = om_all;
     __syncthreads();
-  EPIE_PHASE(5);
+    EPIE_PHASE(5);
   } else {
     __syncthreads();  // red[0] written by thread 0
     omax = red[0];
@@ -254,21 +283,22 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
   EPIE_PHASE(7);
   {
-    // FP32 within a warp, FP64 across warps, CTAs and frames
+    // FP32 within the CTA (lanes, then warps), FP64 across CTAs and frames
+    float *rede = reinterpret_cast<float *>(red + 2);
     const float e = warp_sum_f(mod.e), s = warp_sum_f(isum_t);
     if (lane == 0) {
-      red[2 + warp] = static_cast<double>(e);
-      red[2 + NW + warp] = static_cast<double>(s);
+      rede[2 * warp] = e;
+      rede[2 * warp + 1] = s;
     }
     __syncthreads();
-    if (tid == 0) {
-      double es = 0.0, ss = 0.0;
-      for (int w = 0; w < NW; ++w) {
-        es += red[2 + w];
-        ss += red[2 + NW + w];
+    if (warp == 0) {
+      float es = lane < NW ? rede[2 * lane] : 0.f, ss = lane < NW ? rede[2 * lane + 1] : 0.f;
+      es = warp_sum_f(es);
+      ss = warp_sum_f(ss);
+      if (lane == 0) {
+        a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(es);
+        a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(ss);
       }
-      a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = es;
-      a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] = ss;
     }
   }
   EPIE_PHASE(8);
@@ -313,7 +343,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       for (int i = 0; i < EB; ++i) {
         const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
         pv[i] = __ldg(Pbase + y * N + xl);
-        ov[i] = Obase[y * orow + xl];
+        ov[i] = EPIE_LD_O(Obase + y * orow + xl);
       }
 #pragma unroll
       for (int i = 0; i < EB; ++i) {
@@ -322,7 +352,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
         const float2 d = csub(psi1, cmul(pv[i], ov[i]));
         const float2 uo = cmulc(pv[i], d);  // conj(P) Delta
         const float2 up = cmulc(ov[i], d);  // conj(O_old) Delta
-        Obase[y * orow + xl] = make_float2(fmaf(ao, uo.x, ov[i].x), fmaf(ao, uo.y, ov[i].y));
+        EPIE_ST_O(Obase + y * orow + xl,
+                  make_float2(fmaf(ao, uo.x, ov[i].x), fmaf(ao, uo.y, ov[i].y)));
         part[y * N + xl] = cscale(up, bp);
       }
     }
@@ -349,6 +380,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     // the copy never arrived: give it one more bounded wait before exiting
     mbar_wait_bounded(bar, 0, 100000000ull);
   }
+#undef EPIE_LD_O
+#undef EPIE_ST_O
 #ifdef EPIE_PHASE_CLOCKS
   __syncthreads();
   EPIE_PHASE(13);
