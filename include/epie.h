@@ -111,6 +111,9 @@ typedef struct epie_ctx *epie_t;
 #define EPIE_GEMM_TF32 1     /* tf32 operands                                    */
 #define EPIE_GEMM_BF16X3 2   /* split bf16: hi*hi + hi*lo + lo*hi                */
 #define EPIE_GEMM_FP32EMU 3  /* fp32 emulated on bf16 tensor cores (9 products)  */
+#define EPIE_GEMM_TC_BF16 4  /* bf16 operands, this library's tcgen05 kernel     */
+#define EPIE_GEMM_TC_BF16X3 5 /* split bf16, this library's tcgen05 kernel: the
+                                three products share one TMEM accumulator       */
 
 /* flags */
 #define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
@@ -323,6 +326,24 @@ EPIE_API int epie_amp_loss_grad(const epie_amp_grad_args *args, double *loss);
  * src and dst must not overlap. */
 EPIE_API int epie_frames_to_fft_order(const void *src, void *dst, int32_t n, int32_t N,
                                       int32_t intensity_dtype, void *stream);
+
+/* Tensor-core product, the building block of EPIE_GEMM_TC_*:
+ *   D[M x Nn] = sum over t < terms of A_t[M x K] . B_t[Nn x K]^T
+ * with terms = 1 (A0 B0) or 3 (A0 B0 + A0 B1 + A1 B0, the split-bf16 product
+ * of x = x_hi + x_lo).  The paper (Sec. "ePIE Implementation") runs the
+ * projection through a DFT; a row of N interleaved complex values times the
+ * 2N x 2N real twiddle matrix is that row's DFT, which is how the GEMM path
+ * uses this call.  A_t, B_t: bf16 (uint16 bit patterns), row-major, K
+ * contiguous; D: fp32, row pitch ldd floats.  All pointers are device
+ * pointers, 16-byte aligned; A1 and B1 may be NULL when terms = 1.
+ * M % 128 == 0, Nn % 128 == 0, K % 64 == 0, ldd >= Nn, ldd % 4 == 0, else
+ * EPIE_EINVAL.  `status` is a device int32 the kernel ORs 2 into when one of
+ * its bounded waits (2 s) expires; D is then incomplete.  Asynchronous on
+ * `stream`; allocates nothing.  On failure epie_error(NULL) holds the
+ * reason. */
+EPIE_API int epie_tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1,
+                               float *D, int64_t M, int32_t Nn, int32_t K, int32_t ldd,
+                               int32_t terms, int32_t *status, void *stream);
 
 /* Message of the handle's last error (or of the last failed epie_init in
  * this thread when h is NULL).  Valid until the next call on the handle. */

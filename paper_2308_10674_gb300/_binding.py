@@ -21,6 +21,7 @@ EPIE_SEQUENTIAL, EPIE_COLOURED, EPIE_MINIBATCH = 0, 1, 2
 EPIE_OMAX_PATCH, EPIE_OMAX_GLOBAL = 0, 1
 EPIE_PATH_FUSED, EPIE_PATH_PLAIN, EPIE_PATH_GEMM = 0, 1, 2
 EPIE_GEMM_BF16, EPIE_GEMM_TF32, EPIE_GEMM_BF16X3, EPIE_GEMM_FP32EMU = 0, 1, 2, 3
+EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3 = 4, 5
 EPIE_CHECKED, EPIE_PROBE_SUM, EPIE_GRAPH = 1, 2, 4
 
 STATUS = {0: "EPIE_OK", -1: "EPIE_EINVAL", -2: "EPIE_ERANGE", -3: "EPIE_ECAPACITY",
@@ -92,6 +93,7 @@ def lib():
         L.epie_amp_grad_scratch_bytes.restype = C.c_size_t
         L.epie_amp_loss_grad.argtypes = [C.POINTER(epie_amp_grad_args), C.POINTER(C.c_double)]
         L.epie_frames_to_fft_order.argtypes = [vp, vp, i32, i32, i32, vp]
+        L.epie_tc_gemm_bf16.argtypes = [vp, vp, vp, vp, vp, C.c_int64, i32, i32, i32, i32, vp, vp]
         L.epie_error.argtypes = [H]
         L.epie_error.restype = C.c_char_p
         L.epie_destroy.argtypes = [H]
@@ -298,6 +300,16 @@ def epie_frames_to_fft_order(src_ptr, dst_ptr, n, N, intensity_dtype=EPIE_U16, s
     addresses)."""
     rc = lib().epie_frames_to_fft_order(C.c_void_p(src_ptr), C.c_void_p(dst_ptr), n, N,
                                         intensity_dtype, C.c_void_p(stream) if stream else None)
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
+
+
+def epie_tc_gemm_bf16(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status, stream=None):
+    """D = sum_t A_t B_t^T on the tensor cores (integer device addresses; A1,
+    B1 may be 0 for terms = 1; status: address of a device int32)."""
+    v = lambda x: C.c_void_p(x) if x else None
+    rc = lib().epie_tc_gemm_bf16(v(A0), v(A1), v(B0), v(B1), v(D), M, Nn, K, ldd, terms,
+                                 v(status), v(stream))
     if rc != EPIE_OK:
         raise EpieError(rc, epie_error(None))
 

@@ -17,6 +17,9 @@
 //   EPIE_GEMM_TF32    fp32 operands rounded to tf32 by the tensor cores
 //   EPIE_GEMM_BF16X3  x = x_hi + x_lo in bf16; A B ~ Ah Bh + Ah Bl + Al Bh
 //   EPIE_GEMM_FP32EMU cuBLAS' fp32 emulation on bf16 tensor cores
+//   EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3: the bf16 and split-bf16 products
+//     on this engine's own tcgen05 kernel (epie_tc_gemm.cu), the three
+//     split products accumulated in one tensor-memory accumulator
 // Twiddles are evaluated in double precision on the host (exact k j mod N).
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
@@ -37,6 +40,8 @@ struct GemmPath {
   cublasHandle_t blas = nullptr;
   float *Tf = nullptr, *Ti = nullptr;                       // fp32 forward / inverse, 2N x 2N
   __nv_bfloat16 *Tf_hi = nullptr, *Tf_lo = nullptr, *Ti_hi = nullptr, *Ti_lo = nullptr;
+  // transposed twiddles (K-major B operand of the tcgen05 kernel)
+  __nv_bfloat16 *Tft_hi = nullptr, *Tft_lo = nullptr, *Tit_hi = nullptr, *Tit_lo = nullptr;
   float2 *psi = nullptr, *Y = nullptr;                      // cap * N * N complex each
   __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;           // cap * N * 2N
   double *omax = nullptr;                                   // cap
@@ -130,15 +135,34 @@ cudaError_t split(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long lon
   return cudaGetLastError();
 }
 
+bool tc_precision(int p) { return p == EPIE_GEMM_TC_BF16 || p == EPIE_GEMM_TC_BF16X3; }
+bool split_precision(int p) { return p == EPIE_GEMM_BF16 || p == EPIE_GEMM_BF16X3 || tc_precision(p); }
+bool x3_precision(int p) { return p == EPIE_GEMM_BF16X3 || p == EPIE_GEMM_TC_BF16X3; }
+
 // dst (rows x 2N fp32) = src (rows x 2N) * T, T the 2N x 2N twiddle matrix
 int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool inverse,
-             cudaStream_t st, std::string *err) {
+             int *err_flag, cudaStream_t st, std::string *err) {
   const int n2 = 2 * g->N;
   const float one = 1.f, zero = 0.f;
   const int M = static_cast<int>(rows);
   cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
   const float *srcf = reinterpret_cast<const float *>(src);
   float *dstf = reinterpret_cast<float *>(dst);
+  if (tc_precision(g->precision)) {
+    const bool x3 = g->precision == EPIE_GEMM_TC_BF16X3;
+    cudaError_t e = split(srcf, g->D_hi, x3 ? g->D_lo : nullptr, rows * n2, st);
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return EPIE_ECUDA;
+    }
+    // the kernel takes rows in blocks of 128; the buffers hold an even number
+    // of frames, so the rows past the group (N = 64, odd group) exist and
+    // their results are never read
+    const long long mrows = (rows + 127) / 128 * 128;
+    return tc_gemm_bf16(g->D_hi, x3 ? g->D_lo : nullptr, inverse ? g->Tit_hi : g->Tft_hi,
+                        x3 ? (inverse ? g->Tit_lo : g->Tft_lo) : nullptr, dstf, mrows, n2, n2, n2,
+                        x3 ? 3 : 1, err_flag, st, err);
+  }
   if (g->precision == EPIE_GEMM_TF32 || g->precision == EPIE_GEMM_FP32EMU) {
     const cublasComputeType_t ct = g->precision == EPIE_GEMM_TF32
                                        ? CUBLAS_COMPUTE_32F_FAST_TF32
@@ -190,8 +214,9 @@ int transpose(GemmPath *g, const float2 *src, float2 *dst, int frames, cudaStrea
 void gemm_path_destroy(GemmPath *g) {
   if (!g) return;
   if (g->blas) cublasDestroy(g->blas);
-  void *ptrs[] = {g->Tf, g->Ti, g->Tf_hi, g->Tf_lo, g->Ti_hi, g->Ti_lo,
-                  g->psi, g->Y, g->D_hi, g->D_lo, g->omax};
+  void *ptrs[] = {g->Tf,     g->Ti,     g->Tf_hi,  g->Tf_lo, g->Ti_hi, g->Ti_lo,
+                  g->Tft_hi, g->Tft_lo, g->Tit_hi, g->Tit_lo, g->psi,   g->Y,
+                  g->D_hi,   g->D_lo,   g->omax};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -228,6 +253,23 @@ GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *e
   ok = ok && split(g->Tf, g->Tf_hi, g->Tf_lo, static_cast<long long>(Tf.size()), st) == cudaSuccess &&
        split(g->Ti, g->Ti_hi, g->Ti_lo, static_cast<long long>(Ti.size()), st) == cudaSuccess &&
        cudaStreamSynchronize(st) == cudaSuccess;
+  if (ok && tc_precision(precision)) {
+    // Tt[n][k] = T[k][n]: the twiddle matrix as a K-major B operand
+    std::vector<float> Tft(Tf.size()), Tit(Ti.size());
+    for (int k = 0; k < n2; ++k)
+      for (int n = 0; n < n2; ++n) {
+        Tft[static_cast<size_t>(n) * n2 + k] = Tf[static_cast<size_t>(k) * n2 + n];
+        Tit[static_cast<size_t>(n) * n2 + k] = Ti[static_cast<size_t>(k) * n2 + n];
+      }
+    ok = cudaMalloc(&g->Tft_hi, hb) == cudaSuccess && cudaMalloc(&g->Tft_lo, hb) == cudaSuccess &&
+         cudaMalloc(&g->Tit_hi, hb) == cudaSuccess && cudaMalloc(&g->Tit_lo, hb) == cudaSuccess;
+    // the fp32 buffers are free again once the splits above have run
+    ok = ok && cudaMemcpy(g->Tf, Tft.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(g->Ti, Tit.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+         split(g->Tf, g->Tft_hi, g->Tft_lo, static_cast<long long>(Tf.size()), st) == cudaSuccess &&
+         split(g->Ti, g->Tit_hi, g->Tit_lo, static_cast<long long>(Ti.size()), st) == cudaSuccess &&
+         cudaStreamSynchronize(st) == cudaSuccess;
+  }
   if (!ok) {
     *err = "GEMM path: twiddle matrices could not be set up";
     gemm_path_destroy(g);
@@ -238,7 +280,8 @@ GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *e
 
 int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
   if (members <= g->cap) return EPIE_OK;
-  const int cap = members > 2 * g->cap ? members : 2 * g->cap;
+  int cap = members > 2 * g->cap ? members : 2 * g->cap;
+  cap += cap & 1;  // even: whole 128-row blocks at N = 64
   void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -250,9 +293,9 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
   bool ok = cudaMalloc(&g->psi, sizeof(float2) * K * cap) == cudaSuccess &&
             cudaMalloc(&g->Y, sizeof(float2) * K * cap) == cudaSuccess &&
             cudaMalloc(&g->omax, sizeof(double) * cap) == cudaSuccess;
-  if (ok && (g->precision == EPIE_GEMM_BF16 || g->precision == EPIE_GEMM_BF16X3)) {
+  if (ok && split_precision(g->precision)) {
     ok = cudaMalloc(&g->D_hi, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
-    if (ok && g->precision == EPIE_GEMM_BF16X3)
+    if (ok && x3_precision(g->precision))
       ok = cudaMalloc(&g->D_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
   }
   if (!ok) {
@@ -274,9 +317,9 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
-  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, st, err))) return rc;   // along x
+  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, a.err_flag, st, err))) return rc;   // along x
   if ((rc = transpose(g, g->Y, g->psi, G, st, err))) return rc;
-  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, st, err))) return rc;   // along y
+  if ((rc = rows_dft(g, g->psi, g->Y, rows, false, a.err_flag, st, err))) return rc;   // along y
   dim3 grid(N * N / 1024, G);
   if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, g->Y);
   else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, g->Y);
@@ -285,16 +328,16 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
-  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, st, err))) return rc;    // along y
+  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, a.err_flag, st, err))) return rc;    // along y
   if ((rc = transpose(g, g->psi, g->Y, G, st, err))) return rc;
-  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, st, err))) return rc;    // along x
+  if ((rc = rows_dft(g, g->Y, g->psi, rows, true, a.err_flag, st, err))) return rc;    // along x
   e = a.accO ? launch_mb_accumulate(a, N, g->psi, g->omax, a.accO, a.cnt, st)
              : launch_plain_update(a, N, g->psi, g->omax, st);
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
-  const bool split_launch = g->precision == EPIE_GEMM_BF16 || g->precision == EPIE_GEMM_BF16X3;
+  const bool split_launch = split_precision(g->precision);
   *kernels += 5 + (split_launch ? 4 : 0);  // gather, 2 transposes, modulus, update (+ splits)
   return EPIE_OK;
 }

@@ -55,7 +55,7 @@ struct GroupArgs {
 };
 
 // error-flag bits written by kernels
-enum : int { FLAG_TMA_TIMEOUT = 1 };
+enum : int { FLAG_TMA_TIMEOUT = 1, FLAG_TC_TIMEOUT = 2 };
 
 // fused kernel: one group, dispatch on N and intensity type
 cudaError_t launch_fused(int N, int itype, const GroupArgs &a, cudaStream_t st);
@@ -111,6 +111,12 @@ cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, floa
                             cudaStream_t st);
 
 // tensor-core DFT path (epie_gemm.cu)
+// D[M x Nn] = sum_t A_t B_t^T on the tensor cores (tcgen05, epie_tc_gemm.cu);
+// bf16 operands K-major, fp32 D with row pitch ldd; terms 1 or 3 (split bf16)
+int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
+                 long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
+                 std::string *err);
+
 struct GemmPath;
 GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *err);
 void gemm_path_destroy(GemmPath *g);

@@ -1,0 +1,343 @@
+// epie_tc_gemm.cu -- hand-written tcgen05 GEMM for the DFT-as-GEMM path.
+//
+//   D[M x Nn] (fp32, row pitch ldd) = sum over terms t of A_t[M x K] * B_t[Nn x K]^T
+//
+// A_t and B_t are bf16, row-major with K contiguous (both operands K-major).
+// One term is the plain bf16 product (A0 B0); three terms are the split-bf16
+// product A0 B0 + A0 B1 + A1 B0 (x = x_hi + x_lo), all accumulated in one
+// fp32 accumulator in tensor memory.  In the DFT path A is a block of rows of
+// interleaved complex values and B the transposed 2N x 2N twiddle matrix, so
+// one call is the DFT of every row (Sec. "ePIE Implementation": the
+// projection runs through a DFT of 2^n frames).
+//
+// Kernel design (one CTA = one 128 x BN tile of D, 128 threads):
+//   * operand tiles 128 x 64 (A) and BN x 64 (B) bf16 are fetched by TMA
+//     (cp.async.bulk.tensor.2d, 128-byte swizzle) into a 4-stage ring in
+//     shared memory; mbarrier "full[s]" completes on the copied bytes;
+//   * thread 0 of warp 0 issues the copies; thread 0 of warp 1 issues
+//     tcgen05.mma (M = 128, N = BN, K = 16, kind::f16, bf16 x bf16 -> fp32)
+//     from shared-memory descriptors into a BN-column TMEM accumulator, and
+//     tcgen05.commit on "empty[s]" returns the stage to the producer;
+//   * after the last k-block a final commit completes "done"; each warp then
+//     reads its 32 accumulator rows (TMEM lanes 32w..32w+31) with
+//     tcgen05.ld.32x32b and stores them as 16-byte vectors.
+// Every wait is bounded by %globaltimer (2 s).  On expiry the kernel sets
+// FLAG_TC_TIMEOUT in the status word, skips the epilogue, lets its issued
+// copies land (bounded again), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/epie.h"
+#include "epie_fft.cuh"
+#include "epie_internal.h"
+
+namespace epie {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+
+// ---------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle.  Rows
+// are 128 bytes (64 bf16), eight rows form a 1024-byte swizzle atom and the
+// atoms follow each other along M/N (stride byte offset 1024).  The leading
+// byte offset is unused for a swizzled K-major tile whose K extent is one
+// swizzle width.  Bits: start address >> 4 [0,14), LBO >> 4 [16,30),
+// SBO >> 4 [32,46), descriptor version 1 [46,48), swizzle mode 2 = 128 B
+// [61,64).
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
+         (static_cast<uint64_t>(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator [4,6) = 1, A and B
+// bf16 [7,10) = [10,13) = 1, both K-major (bits 15, 16 clear), N >> 3 at
+// [17,23), M >> 4 at [24,29).
+template <int M, int N>
+__host__ __device__ constexpr uint32_t f16_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's accumulator row
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+struct TcCfg {
+  static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr size_t OFF_BAR = static_cast<size_t>(TC_STAGES) * STAGE;
+  // full[S], empty[S], done, then the TMEM address slot and the abort word
+  static constexpr size_t SMEM = 1024 + OFF_BAR + 8 * (2 * TC_STAGES + 1) + 16;
+  static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms stay aligned");
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                   const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                   float *__restrict__ D, int ldd, int K, int terms, int *err_flag) {
+  using C = TcCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  // 128-byte-swizzled tiles want 1024-byte alignment
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+  uint64_t *empty = full + TC_STAGES;
+  uint64_t *done = empty + TC_STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_word = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+  const int kb_term = K / TC_BK, nkb = kb_term * terms;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_word = 0;
+    fence_mbar_init();
+  }
+  if (warp == 2) tmem_alloc(tmem_slot, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: TMA copies of the operand tiles
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES, u = kb / TC_STAGES;
+      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], (u - 1) & 1, TC_WAIT_NS)) {
+        *abort_word = 1;
+        atomicOr(err_flag, FLAG_TC_TIMEOUT);
+        break;
+      }
+      if (*abort_word) break;
+      const int t = kb / kb_term, kx = (kb % kb_term) * TC_BK;
+      const CUtensorMap *ma = t == 2 ? &mA1 : &mA0;  // terms: A0 B0, A0 B1, A1 B0
+      const CUtensorMap *mb = t == 1 ? &mB1 : &mB0;
+      uint8_t *sa = smem + static_cast<size_t>(s) * C::STAGE;
+      mbar_arrive_expect_tx(&full[s], C::STAGE);
+      tma_load_2d(sa, ma, kx, m0, &full[s]);
+      tma_load_2d(sa + C::A_BYTES, mb, kx, n0, &full[s]);
+      issued = kb + 1;
+    }
+    // every issued copy has landed before the CTA can exit
+    for (int kb = issued - TC_STAGES < 0 ? 0 : issued - TC_STAGES; kb < issued; ++kb)
+      if (!mbar_wait_bounded(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1, TC_WAIT_NS)) {
+        *abort_word = 1;
+        atomicOr(err_flag, FLAG_TC_TIMEOUT);
+      }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = f16_idesc<TC_BM, BN>();
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES, u = kb / TC_STAGES;
+      if (!mbar_wait_bounded(&full[s], u & 1, TC_WAIT_NS)) {
+        *abort_word = 1;
+        atomicOr(err_flag, FLAG_TC_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_addr = smem_u32(smem + static_cast<size_t>(s) * C::STAGE);
+      const uint32_t b_addr = a_addr + C::A_BYTES;
+#pragma unroll
+      for (int k = 0; k < TC_BK / 16; ++k)  // K = 16 per instruction: 32 bytes along the row
+        umma_f16(tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
+                 idesc, (kb | k) != 0);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);  // arrives once every issued MMA has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue: TMEM -> registers -> global
+  bool ok = mbar_wait_bounded(done, 0, TC_WAIT_NS);
+  ok = __all_sync(0xffffffffu, ok) && !*abort_word;
+  tc_fence_after();
+  if (ok) {
+    float *drow = D + static_cast<size_t>(m0 + warp * 32 + lane) * ldd + n0;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tlane + c, r);
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4 *>(drow + c + j) =
+            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                        __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+    }
+  } else if (lane == 0) {
+    atomicOr(err_flag, FLAG_TC_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tmem_dealloc(tmem, BN);
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder(std::string *err) {
+  static EncodeTiled fn = nullptr;
+  if (fn) return fn;
+  void *p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p) {
+    *err = "cuTensorMapEncodeTiled is not available from the driver";
+    return nullptr;
+  }
+  fn = reinterpret_cast<EncodeTiled>(p);
+  return fn;
+}
+
+// rows x K bf16, row-major; box = box_rows x 64, 128-byte swizzle
+bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_rows,
+              std::string *err) {
+  EncodeTiled enc = encoder(err);
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *err = "cuTensorMapEncodeTiled failed (" + std::to_string(static_cast<int>(r)) + ")";
+    return false;
+  }
+  return true;
+}
+
+template <int BN>
+cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
+                      const CUtensorMap &b1, float *D, long long M, int Nn, int K, int ldd,
+                      int terms, int *err_flag, cudaStream_t st) {
+  using C = TcCfg<BN>;
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(C::SMEM));
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  dim3 grid(static_cast<unsigned>(M / TC_BM), static_cast<unsigned>(Nn / BN));
+  tc_gemm_kernel<BN><<<grid, 128, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms, err_flag);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
+                 long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
+                 std::string *err) {
+  const int BN = Nn % 256 == 0 ? 256 : 128;
+  if (!A0 || !B0 || !D || !err_flag || (terms != 1 && terms != 3) ||
+      (terms == 3 && (!A1 || !B1))) {
+    *err = "tc_gemm_bf16: null operand, or terms not 1 or 3";
+    return EPIE_EINVAL;
+  }
+  if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % TC_BK || ldd < Nn ||
+      ldd % 4 || M / TC_BM > 0x7fffffffLL) {
+    *err = "tc_gemm_bf16: M must be a positive multiple of 128, Nn of 128, K of 64, "
+           "ldd >= Nn and a multiple of 4";
+    return EPIE_EINVAL;
+  }
+  const void *ptrs[5] = {A0, A1 ? A1 : A0, B0, B1 ? B1 : B0, D};
+  for (const void *p : ptrs)
+    if (reinterpret_cast<uintptr_t>(p) % 16) {
+      *err = "tc_gemm_bf16: operands must be 16-byte aligned";
+      return EPIE_EINVAL;
+    }
+  CUtensorMap a0, a1, b0, b1;
+  if (!make_map(&a0, A0, M, K, TC_BM, err) || !make_map(&a1, A1 ? A1 : A0, M, K, TC_BM, err) ||
+      !make_map(&b0, B0, Nn, K, BN, err) || !make_map(&b1, B1 ? B1 : B0, Nn, K, BN, err))
+    return EPIE_ECUDA;
+  cudaError_t e = BN == 256 ? launch_tc<256>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
+                            : launch_tc<128>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  return EPIE_OK;
+}
+
+}  // namespace epie

@@ -118,3 +118,15 @@ def test_null_handle_calls_are_rejected(B):
     assert L.epie_destroy(None) == B.EPIE_OK
     n = ctypes.c_int32()
     assert L.epie_num_frames(None, ctypes.byref(n)) == B.EPIE_EINVAL
+
+
+@pytest.mark.parametrize("M,Nn,K,ldd,terms", [
+    (100, 256, 64, 256, 1), (128, 200, 64, 256, 1), (128, 256, 96, 256, 1),
+    (128, 256, 64, 255, 1), (128, 256, 64, 256, 2), (128, 256, 64, 128, 1),
+])
+def test_tc_gemm_rejects_bad_shapes_on_the_host(B, M, Nn, K, ldd, terms):
+    """Shape checks of the tensor-core product run before any device call."""
+    fake = 1 << 20  # 16-byte aligned, never dereferenced
+    with pytest.raises(B.EpieError) as ex:
+        B.epie_tc_gemm_bf16(fake, fake, fake, fake, fake, M, Nn, K, ldd, terms, fake)
+    assert ex.value.code == B.EPIE_EINVAL
