@@ -345,6 +345,16 @@ EPIE_API int epie_tc_gemm_bf16(const void *A0, const void *A1, const void *B0, c
                                float *D, int64_t M, int32_t Nn, int32_t K, int32_t ldd,
                                int32_t terms, int32_t *status, void *stream);
 
+/* FP32 FMA throughput of `device`: a kernel of independent FMA chains on
+ * every SM (8 blocks of 256 threads per SM, `iters` x 256 FMAs per thread,
+ * about 35 ms per 1000 iters on a GB300) after one short warm-up launch.
+ * *tflops = 2 x FMAs / elapsed time; *sm_mhz = the SM clock during the run
+ * (clock64 over %globaltimer on one SM).  This is the measured roofline
+ * denominator of the fused step, whose transforms run on the FP32 pipes;
+ * the paper has no counterpart.  Synchronous; EPIE_EINVAL for iters < 1 or
+ * NULL outputs. */
+EPIE_API int epie_fp32_fma_peak(int32_t device, int32_t iters, double *tflops, double *sm_mhz);
+
 /* Message of the handle's last error (or of the last failed epie_init in
  * this thread when h is NULL).  Valid until the next call on the handle. */
 EPIE_API const char *epie_error(epie_t h);

@@ -94,6 +94,7 @@ def lib():
         L.epie_amp_loss_grad.argtypes = [C.POINTER(epie_amp_grad_args), C.POINTER(C.c_double)]
         L.epie_frames_to_fft_order.argtypes = [vp, vp, i32, i32, i32, vp]
         L.epie_tc_gemm_bf16.argtypes = [vp, vp, vp, vp, vp, C.c_int64, i32, i32, i32, i32, vp, vp]
+        L.epie_fp32_fma_peak.argtypes = [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.epie_error.argtypes = [H]
         L.epie_error.restype = C.c_char_p
         L.epie_destroy.argtypes = [H]
@@ -312,6 +313,15 @@ def epie_tc_gemm_bf16(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status, stream=No
                                  v(status), v(stream))
     if rc != EPIE_OK:
         raise EpieError(rc, epie_error(None))
+
+
+def epie_fp32_fma_peak(device=0, iters=4096):
+    """(TFLOP/s, SM MHz) of an FP32 FMA-chain kernel on the device."""
+    t, m = C.c_double(), C.c_double()
+    rc = lib().epie_fp32_fma_peak(device, iters, C.byref(t), C.byref(m))
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
+    return t.value, m.value
 
 
 def epie_amp_grad_scratch_bytes(N, n):

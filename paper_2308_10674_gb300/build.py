@@ -17,7 +17,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXTRA = os.environ.get("EPIE_NVCC_FLAGS", "").split()
 SOURCES = ["epie_abi.cpp", "epie_dispatch.cu", "epie_aux.cu", "epie_fused_64.cu",
            "epie_fused_128.cu", "epie_fused_256.cu", "epie_fused_512.cu", "epie_static.cu",
-           "epie_adjoint.cu", "epie_gemm.cu", "epie_tc_gemm.cu"]
+           "epie_adjoint.cu", "epie_gemm.cu", "epie_tc_gemm.cu",
+           "epie_peak.cu"]
 
 
 def nvcc() -> str:

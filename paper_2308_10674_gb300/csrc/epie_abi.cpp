@@ -266,7 +266,8 @@ int get_plan(epie_ctx *h, int batch, cufftHandle *out) {
 }
 
 // One group: fused kernel (or the plain sequence), then the probe reduction.
-int run_group(epie_ctx *h, const int32_t *members_d, int n_members, int64_t *kernels) {
+int run_group(epie_ctx *h, const int32_t *members_d, int n_members, bool o_early,
+              int64_t *kernels) {
   const int N = h->cfg.N;
   int rc = ensure_part(h, n_members);
   if (rc) return rc;
@@ -292,6 +293,7 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, int64_t *ker
   a.err_flag = h->flag_d;
   a.accO = mb ? h->accO : nullptr;
   a.cnt = mb ? h->cnt : nullptr;
+  a.o_early = o_early && !h->ktime;  // timing events sit between the launches
   if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
     CK(epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st));
     a.omax2_global = h->omax_glob;
@@ -425,6 +427,7 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
       a.err_flag = h->flag_d;
       a.accO = mb ? h->accO : nullptr;
       a.cnt = mb ? h->cnt : nullptr;
+      a.o_early = g > 0;
       if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
         ce = epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st);
         a.omax2_global = h->omax_glob;
@@ -483,7 +486,7 @@ int run_sweep(epie_ctx *h, int slot, int64_t *kernels) {
   for (int g = 0; g < ng; ++g) {
     const int m = gstart[g + 1] - gstart[g];
     if (m == 0) continue;
-    int rc = run_group(h, h->order_d + gstart[g], m, kernels);
+    int rc = run_group(h, h->order_d + gstart[g], m, g > 0, kernels);
     if (rc) return rc;
   }
   CK(epie::launch_error_reduce(h->err_part, h->isum_part, n, h->err_stride, h->err_out + slot,
@@ -1143,6 +1146,17 @@ int epie_tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void
   const int rc = epie::tc_gemm_bf16(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status,
                                     static_cast<cudaStream_t>(stream), &why);
   if (rc) g_init_error = "epie_tc_gemm_bf16: " + why;
+  return rc;
+}
+
+int epie_fp32_fma_peak(int32_t device, int32_t iters, double *tflops, double *sm_mhz) {
+  if (iters < 1 || !tflops || !sm_mhz) {
+    g_init_error = "epie_fp32_fma_peak: iters must be >= 1 and the outputs non-NULL";
+    return EPIE_EINVAL;
+  }
+  std::string why;
+  const int rc = epie::fma_peak(device, iters, tflops, sm_mhz, &why);
+  if (rc) g_init_error = "epie_fp32_fma_peak: " + why;
   return rc;
 }
 

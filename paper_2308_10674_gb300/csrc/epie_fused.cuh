@@ -149,11 +149,6 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
                   l2_evict_first_policy());
   }
   for (int m = tid; m < N; m += NT) tw[m] = a.twiddle[m];
-  // everything above reads data written before the sweep; the object, probe,
-  // max|P|^2 and the partial buffers are written by the preceding kernels
-  grid_dependency_wait();
-  grid_dependents_launch();
-  if (blockIdx.x == 0 && tid == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
 
   // ---------------------------------------------------------------- phase 1
   const size_t orow = static_cast<size_t>(a.W);
@@ -175,21 +170,48 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
 #define EPIE_LD_O(p) (*(p))
 #define EPIE_ST_O(p, v) (*(p) = (v))
 #endif
+  // the object patch goes to the tile (and its maximum is found) before the
+  // dependency wait when o_early says it is final, after it otherwise; the
+  // probe, written by the preceding reduction, is applied after the wait
+  auto load_patch = [&]() {
+#pragma unroll
+    for (int i0 = 0; i0 < E; i0 += EB) {
+      float2 ov[EB];
+#pragma unroll
+      for (int i = 0; i < EB; ++i) {
+        const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+        ov[i] = EPIE_LD_O(Obase + y * orow + xl);
+      }
+#pragma unroll
+      for (int i = 0; i < EB; ++i) {
+        const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
+        const float q = ov[i].x * ov[i].x + ov[i].y * ov[i].y;
+        if (q > om) { om = q; omv = ov[i]; }
+        slab[ColA::at(xl, y)] = ov[i];
+      }
+    }
+  };
+  if (a.o_early) load_patch();
+  // everything above reads data written before the sweep (or, with o_early,
+  // an object no kernel still running writes); the probe, max|P|^2 and the
+  // partial buffers are written by the preceding kernels
+  grid_dependency_wait();
+  grid_dependents_launch();
+  if (blockIdx.x == 0 && tid == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
+  if (!a.o_early) load_patch();
 #pragma unroll
   for (int i0 = 0; i0 < E; i0 += EB) {
-    float2 pv[EB], ov[EB];
+    float2 pv[EB];
 #pragma unroll
     for (int i = 0; i < EB; ++i) {
       const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
       pv[i] = __ldg(Pbase + y * N + xl);
-      ov[i] = EPIE_LD_O(Obase + y * orow + xl);
     }
 #pragma unroll
     for (int i = 0; i < EB; ++i) {
       const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
-      const float q = ov[i].x * ov[i].x + ov[i].y * ov[i].y;
-      if (q > om) { om = q; omv = ov[i]; }
-      slab[ColA::at(xl, y)] = cmul(pv[i], ov[i]);
+      float2 &t = slab[ColA::at(xl, y)];  // written by this thread above
+      t = cmul(pv[i], t);
     }
   }
   __syncthreads();

@@ -52,6 +52,10 @@ struct GroupArgs {
   // the grid is sized for the largest group; surplus clusters exit at once
   const int32_t *gstart;
   int group;
+  // 1 when the launch follows the probe reduction of the previous group of
+  // the same sweep: that reduction waited for the previous step kernel, so
+  // the object is final and may be read before this kernel's dependency wait
+  int o_early;
 };
 
 // error-flag bits written by kernels
@@ -116,6 +120,9 @@ cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, floa
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err);
+
+// FP32 FMA-chain throughput (epie_peak.cu)
+int fma_peak(int device, int iters, double *tflops, double *sm_mhz, std::string *err);
 
 struct GemmPath;
 GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *err);

@@ -130,3 +130,10 @@ def test_tc_gemm_rejects_bad_shapes_on_the_host(B, M, Nn, K, ldd, terms):
     with pytest.raises(B.EpieError) as ex:
         B.epie_tc_gemm_bf16(fake, fake, fake, fake, fake, M, Nn, K, ldd, terms, fake)
     assert ex.value.code == B.EPIE_EINVAL
+
+
+def test_fma_peak_rejects_bad_arguments(B):
+    import ctypes
+    t, m = ctypes.c_double(), ctypes.c_double()
+    assert B.lib().epie_fp32_fma_peak(0, 0, ctypes.byref(t), ctypes.byref(m)) == B.EPIE_EINVAL
+    assert B.lib().epie_fp32_fma_peak(0, 10, None, ctypes.byref(m)) == B.EPIE_EINVAL

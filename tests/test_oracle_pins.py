@@ -281,6 +281,43 @@ def test_coloured_equals_sequential_when_classes_are_single(orc):
     assert rel(Oa, Ob) <= 1e-14 and rel(Pa, Pb) <= 1e-14
 
 
+def test_parallel_one_subset_is_the_plain_sweep(orc):
+    """The paper's parallel scheme with a single subset: R rounds of k sweeps
+    are R*k plain sweeps (catches a sweep counter that restarts every round,
+    or a wrong order stream)."""
+    N = 16
+    pos, I_all, O0, P0 = _sparse_instance(N)
+    Oa, Pa = O0.copy(), P0.copy()
+    orc.run_parallel_average(Oa, Pa, I_all, pos, [np.arange(len(pos))], 2, 3, N, seed=4)
+    Ob, Pb = O0.copy(), P0.copy()
+    orc.run_sweeps(Ob, Pb, I_all, pos, 6, N, seed=4)
+    assert np.array_equal(Oa, Ob) and np.array_equal(Pa, Pb)
+
+
+def test_parallel_average_of_disjoint_positions_is_a_half_step(orc):
+    """Two subsets of one position each, patches disjoint, beta = 0: each copy
+    moves only its own patch, and the object update is linear in alpha, so
+    the average equals one sequential sweep over both positions with alpha/2
+    (catches copies that share state, a missing or wrong divisor).  Two
+    copies of the same position average to that position's single step."""
+    N = 16
+    pos, I_all, O0, P0 = _sparse_instance(N, step=N + 2)
+    a, b = 0, len(pos) - 1
+    assert abs(int(pos[a, 0]) - int(pos[b, 0])) >= N or abs(int(pos[a, 1]) - int(pos[b, 1])) >= N
+    Op, Pp = O0.copy(), P0.copy()
+    orc.run_parallel_average(Op, Pp, I_all, pos, [np.array([a]), np.array([b])], 1, 1, N,
+                             seed=2, beta=0.0)
+    Oh, Ph = O0.copy(), P0.copy()
+    two = np.array([a, b])
+    orc.run_sweeps(Oh, Ph, I_all[two], pos[two], 1, N, seed=7, alpha=0.5, beta=0.0)
+    assert rel(Op, Oh) <= 1e-14 and np.array_equal(Pp, P0) and not np.array_equal(Op, O0)
+    Os, Ps = O0.copy(), P0.copy()
+    orc.run_parallel_average(Os, Ps, I_all, pos, [np.array([a]), np.array([a])], 1, 1, N, seed=2)
+    O1, P1 = O0.copy(), P0.copy()
+    orc.run_sweeps(O1, P1, I_all[[a]], pos[[a]], 1, N, seed=0)
+    assert rel(Os, O1) <= 1e-15 and rel(Ps, P1) <= 1e-15
+
+
 def test_group_members_must_not_overlap(orc):
     N = 16
     pos, I_all, O0, P0 = _sparse_instance(N)
