@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--workload", default="live",
-                    choices=["live", "multiscan", "adjoint", "live-schedule"],
+                    choices=["live", "multiscan", "adjoint", "live-schedule", "tc-gemm"],
                     help="live: the headline 256^2 live scan; multiscan: eight uneven scans "
                          "sweeping concurrently; adjoint: amplitude-loss gradients at 128^2; "
-                         "live-schedule: the whole live run, chunk by chunk")
+                         "live-schedule: the whole live run, chunk by chunk; tc-gemm: the "
+                         "tcgen05 GEMM of the DFT-as-GEMM path on its shapes")
     ap.add_argument("--sweeps-per-chunk", type=int, default=50,
                     help="live-schedule: sweeps after each chunk (and at the end)")
     return ap.parse_args()
@@ -634,6 +635,84 @@ def run_live_schedule(args):
     return 0
 
 
+TC_SHAPES = [(262144, 512, 512, "256^2 DFT rows, 1024 frames"),
+             (131072, 256, 256, "128^2 DFT rows, 1024 frames"),
+             (65536, 1024, 1024, "512^2 DFT rows, 128 frames"),
+             (16384, 4096, 4096, "square")]
+
+
+def run_tc_gemm(args):
+    """The engine's tcgen05 GEMM (epie_tc_gemm_bf16, D = sum_t A_t B_t^T, bf16
+    operands, fp32 accumulation and output) on the DFT-as-GEMM path's shapes,
+    one and three (split bf16) terms, against cuBLAS bf16 (torch.matmul).
+    The headline line is the 256^2 DFT shape with three terms."""
+    import torch
+    from paper_2308_10674_gb300 import _binding as B
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    pk, pk_kind = peaks()
+    st = torch.cuda.current_stream().cuda_stream
+    rows, launches = [], 0
+
+    def timed(f, reps):
+        for _ in range(max(3, args.warmup)):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with Clocks(0) as clk:
+        for M, Nn, K, what in TC_SHAPES:
+            g = torch.Generator(device=dev).manual_seed(M + Nn)
+            A0 = torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16)
+            A1 = (torch.randn(M, K, device=dev, generator=g) * 2 ** -8).to(torch.bfloat16)
+            B0 = torch.randn(Nn, K, device=dev, generator=g).to(torch.bfloat16)
+            B1 = (torch.randn(Nn, K, device=dev, generator=g) * 2 ** -8).to(torch.bfloat16)
+            D = torch.empty(M, Nn, device=dev)
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+            for terms in (1, 3):
+                f = lambda: B.epie_tc_gemm_bf16(A0.data_ptr(), A1.data_ptr(), B0.data_ptr(),
+                                                B1.data_ptr(), D.data_ptr(), M, Nn, K, Nn, terms,
+                                                status.data_ptr(), st)
+                ms = timed(f, args.steps * 2)
+                launches += args.steps * 2
+                if int(status.item()):
+                    raise RuntimeError("tcgen05 GEMM reported a wait time-out")
+                nbytes = M * K * 2 * (2 if terms == 3 else 1) + Nn * K * 2 * 2 + M * Nn * 4
+                rows.append({"shape": [M, Nn, K], "what": what, "terms": terms, "ms": ms,
+                             "tflops": 2.0 * M * Nn * K * terms / ms / 1e9,
+                             "hbm_gbs": nbytes / ms / 1e6})
+            ms = timed(lambda: torch.matmul(A0, B0.t()), args.steps * 2)
+            rows.append({"shape": [M, Nn, K], "what": what, "cublas_bf16_ms": ms,
+                         "tflops": 2.0 * M * Nn * K / ms / 1e9})
+            del A0, A1, B0, B1, D
+            torch.cuda.empty_cache()
+    head = rows[1]  # 256^2 DFT rows, three terms
+    M, Nn, K = head["shape"]
+    line = {"metric": "tcgen05 DFT-as-GEMM, 256^2 rows of 1024 frames, split-bf16 (3 products)",
+            "value": head["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps * 2,
+            "warmup": max(3, args.warmup), "ms_per_step": head["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "D = A B^T, A 262144x512, B 512x512 bf16, fp32 D",
+                       "l2": "inputs larger than L2"},
+            "clocks": clk.summary(), "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": head["hbm_gbs"], "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": head["hbm_gbs"] / pk["hbm_gbs"], "traffic": None,
+                         "peak_kind": pk_kind,
+                         "tensor": {"achieved_tflops": head["tflops"],
+                                    "peak_tflops": pk.get("bf16_tflops"),
+                                    "frac": head["tflops"] / pk["bf16_tflops"]
+                                    if pk.get("bf16_tflops") else None}},
+            "shapes": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -644,6 +723,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "live-schedule":
         return run_live_schedule(args)
+    if args.workload == "tc-gemm":
+        return run_tc_gemm(args)
     return run_ours(args)
 
 

@@ -124,123 +124,180 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
 template <int BN>
 struct TcCfg {
   static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
   static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
   static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
   static constexpr size_t OFF_BAR = static_cast<size_t>(TC_STAGES) * STAGE;
-  // full[S], empty[S], done, then the TMEM address slot and the abort word
-  static constexpr size_t SMEM = 1024 + OFF_BAR + 8 * (2 * TC_STAGES + 1) + 16;
+  // full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then the TMEM
+  // address slot and the abort word
+  static constexpr int NBAR = 2 * TC_STAGES + 5;
+  static constexpr size_t SMEM = 1024 + OFF_BAR + 8 * NBAR + 16;
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms stay aligned");
 };
 
+constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA (owns TMEM), warps 2-5 epilogue
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... (tile t = row block
+// t / n_tiles, column block t % n_tiles, so neighbouring CTAs share the row
+// block in L2).  Two accumulators of BN columns alternate in TMEM: the
+// epilogue drains tile i while the MMAs of tile i + 1 run.
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-                   float *__restrict__ D, int ldd, int K, int terms, int *err_flag) {
+                   float *__restrict__ D, int ldd, int K, int terms, int m_tiles, int n_tiles,
+                   int *err_flag) {
   using C = TcCfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   // 128-byte-swizzled tiles want 1024-byte alignment
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
   uint64_t *empty = full + TC_STAGES;
-  uint64_t *done = empty + TC_STAGES;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  uint64_t *acc_full = empty + TC_STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *mma_done = acc_empty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_word = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
   const int kb_term = K / TC_BK, nkb = kb_term * terms;
+  const int tiles = m_tiles * n_tiles;
+  auto fail = [&]() {
+    *abort_word = 1;
+    atomicOr(err_flag, FLAG_TC_TIMEOUT);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(mma_done, 1);
     *abort_word = 0;
     fence_mbar_init();
   }
-  if (warp == 2) tmem_alloc(tmem_slot, BN);
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- producer: TMA copies of the operand tiles
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES, u = kb / TC_STAGES;
-      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], (u - 1) & 1, TC_WAIT_NS)) {
-        *abort_word = 1;
-        atomicOr(err_flag, FLAG_TC_TIMEOUT);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: TMA copies of the operand tiles, k-block after k-block
+      int it = 0;
+      for (int tile = blockIdx.x; tile < tiles && !*abort_word; tile += gridDim.x) {
+        const int m0 = (tile / n_tiles) * TC_BM, n0 = (tile % n_tiles) * BN;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % TC_STAGES, u = it / TC_STAGES;
+          if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], (u - 1) & 1, TC_WAIT_NS)) {
+            fail();
+            break;
+          }
+          if (*abort_word) break;
+          const int t = kb / kb_term, kx = (kb % kb_term) * TC_BK;
+          const CUtensorMap *ma = t == 2 ? &mA1 : &mA0;  // terms: A0 B0, A0 B1, A1 B0
+          const CUtensorMap *mb = t == 1 ? &mB1 : &mB0;
+          uint8_t *sa = smem + static_cast<size_t>(s) * C::STAGE;
+          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          tma_load_2d(sa, ma, kx, m0, &full[s]);
+          tma_load_2d(sa + C::A_BYTES, mb, kx, n0, &full[s]);
+          ++it;
+        }
       }
-      if (*abort_word) break;
-      const int t = kb / kb_term, kx = (kb % kb_term) * TC_BK;
-      const CUtensorMap *ma = t == 2 ? &mA1 : &mA0;  // terms: A0 B0, A0 B1, A1 B0
-      const CUtensorMap *mb = t == 1 ? &mB1 : &mB0;
-      uint8_t *sa = smem + static_cast<size_t>(s) * C::STAGE;
-      mbar_arrive_expect_tx(&full[s], C::STAGE);
-      tma_load_2d(sa, ma, kx, m0, &full[s]);
-      tma_load_2d(sa + C::A_BYTES, mb, kx, n0, &full[s]);
-      issued = kb + 1;
+      // every issued copy has landed before the CTA can exit
+      for (int j = it - TC_STAGES < 0 ? 0 : it - TC_STAGES; j < it; ++j)
+        if (!mbar_wait_bounded(&full[j % TC_STAGES], (j / TC_STAGES) & 1, TC_WAIT_NS)) fail();
     }
-    // every issued copy has landed before the CTA can exit
-    for (int kb = issued - TC_STAGES < 0 ? 0 : issued - TC_STAGES; kb < issued; ++kb)
-      if (!mbar_wait_bounded(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1, TC_WAIT_NS)) {
-        *abort_word = 1;
-        atomicOr(err_flag, FLAG_TC_TIMEOUT);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = f16_idesc<TC_BM, BN>();
+      int it = 0, tl = 0;
+      for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
+        if (*abort_word) break;
+        const int b = tl & 1, ub = tl >> 1;
+        if (tl >= 2 && !mbar_wait_bounded(&acc_empty[b], (ub - 1) & 1, TC_WAIT_NS)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + static_cast<uint32_t>(b * BN);
+        bool bad = false;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % TC_STAGES, u = it / TC_STAGES;
+          if (!mbar_wait_bounded(&full[s], u & 1, TC_WAIT_NS)) {
+            fail();
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(smem + static_cast<size_t>(s) * C::STAGE);
+          const uint32_t b_addr = a_addr + C::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < TC_BK / 16; ++k)  // K = 16 per instruction: 32 bytes along the row
+            umma_f16(acc, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
+                     idesc, (kb | k) != 0);
+          umma_commit(&empty[s]);
+        }
+        if (bad) break;
+        umma_commit(&acc_full[b]);
       }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = f16_idesc<TC_BM, BN>();
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES, u = kb / TC_STAGES;
-      if (!mbar_wait_bounded(&full[s], u & 1, TC_WAIT_NS)) {
-        *abort_word = 1;
-        atomicOr(err_flag, FLAG_TC_TIMEOUT);
+      // every issued MMA has finished before the teardown frees the TMEM
+      umma_commit(mma_done);
+      if (!mbar_wait_bounded(mma_done, 0, TC_WAIT_NS)) fail();
+    }
+  } else {
+    // ---- epilogue: TMEM -> registers -> global; warp w reads TMEM lanes
+    // 32 (w % 4) .. 32 (w % 4) + 31, i.e. rows of that quadrant of the tile
+    const int q = warp & 3;
+    int tl = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
+      const int b = tl & 1, ub = tl >> 1;
+      bool ok = mbar_wait_bounded(&acc_full[b], ub & 1, TC_WAIT_NS);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok || *abort_word) {
+        if (!ok && lane == 0) fail();
         break;
       }
       tc_fence_after();
-      const uint32_t a_addr = smem_u32(smem + static_cast<size_t>(s) * C::STAGE);
-      const uint32_t b_addr = a_addr + C::A_BYTES;
+      const int m0 = (tile / n_tiles) * TC_BM, n0 = (tile % n_tiles) * BN;
+      float *drow = D + static_cast<size_t>(m0 + 32 * q + lane) * ldd + n0;
+      const uint32_t tq = tmem + static_cast<uint32_t>(b * BN) + (static_cast<uint32_t>(32 * q) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tq + c, r);
 #pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k)  // K = 16 per instruction: 32 bytes along the row
-        umma_f16(tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
-                 idesc, (kb | k) != 0);
-      umma_commit(&empty[s]);
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4 *>(drow + c + j) =
+              make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                          __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-    umma_commit(done);  // arrives once every issued MMA has completed
   }
   __syncwarp();
-
-  // ---- epilogue: TMEM -> registers -> global
-  bool ok = mbar_wait_bounded(done, 0, TC_WAIT_NS);
-  ok = __all_sync(0xffffffffu, ok) && !*abort_word;
-  tc_fence_after();
-  if (ok) {
-    float *drow = D + static_cast<size_t>(m0 + warp * 32 + lane) * ldd + n0;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(tlane + c, r);
-#pragma unroll
-      for (int j = 0; j < 32; j += 4)
-        *reinterpret_cast<float4 *>(drow + c + j) =
-            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                        __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-    }
-  } else if (lane == 0) {
-    atomicOr(err_flag, FLAG_TC_TIMEOUT);
-  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) tmem_dealloc(tmem, BN);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * BN);
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -289,18 +346,22 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
                       const CUtensorMap &b1, float *D, long long M, int Nn, int K, int ldd,
                       int terms, int *err_flag, cudaStream_t st) {
   using C = TcCfg<BN>;
-  static int attr_dev = -1;
+  static int attr_dev = -1, sms = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(C::SMEM));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  dim3 grid(static_cast<unsigned>(M / TC_BM), static_cast<unsigned>(Nn / BN));
-  tc_gemm_kernel<BN><<<grid, 128, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms, err_flag);
+  const int m_tiles = static_cast<int>(M / TC_BM), n_tiles = Nn / BN;
+  const long long tiles = static_cast<long long>(m_tiles) * n_tiles;
+  const int grid = static_cast<int>(tiles < sms ? tiles : sms);  // one CTA per SM
+  tc_gemm_kernel<BN><<<grid, TC_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms, m_tiles,
+                                                          n_tiles, err_flag);
   return cudaGetLastError();
 }
 
@@ -316,7 +377,7 @@ int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1,
     return EPIE_EINVAL;
   }
   if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % TC_BK || ldd < Nn ||
-      ldd % 4 || M / TC_BM > 0x7fffffffLL) {
+      ldd % 4 || (M / TC_BM) * (Nn / 128) > 0x7fffffffLL) {
     *err = "tc_gemm_bf16: M must be a positive multiple of 128, Nn of 128, K of 64, "
            "ldd >= Nn and a multiple of 4";
     return EPIE_EINVAL;
