@@ -119,6 +119,10 @@ typedef struct epie_ctx *epie_t;
 #define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
                                 the sweep error is not finite                   */
 #define EPIE_PROBE_SUM 2u    /* coloured: probe moves by the sum, not the mean  */
+#define EPIE_FRAMES_FFT_ORDER 8u /* frames and dark field arrive in FFT order (zero
+                                frequency at [0,0]) and are stored as given;
+                                without it they are DC-centred (the detector's
+                                layout) and re-laid out on the device         */
 #define EPIE_GRAPH 4u        /* fused path: capture a sweep's launches in a CUDA
                                 graph once and replay it each sweep (the group
                                 table is uploaded per sweep; recaptured when the

@@ -599,7 +599,8 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_TC_BF16X3)
     why = "bad gemm_precision";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
-  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH)) why = "unknown flags";
+  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH | EPIE_FRAMES_FFT_ORDER))
+    why = "unknown flags";
   else if (c.class_cap < 0) why = "class_cap must be >= 0";
   if (!why.empty()) {
     g_init_error = "epie_init: " + why;
@@ -741,9 +742,13 @@ int epie_set_dark(epie_t h, const float *dark) {
   }
   float *tmp = reinterpret_cast<float *>(h->stage_d);
   CK(cudaStreamWaitEvent(h->st, h->ev_up, 0));
-  CK(cudaMemcpyAsync(tmp, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
-  CK(epie::launch_dark_ingest(tmp, h->dark_d, h->cfg.N, h->st));
-  h->launches_total += 1;
+  if (h->cfg.flags & EPIE_FRAMES_FFT_ORDER) {
+    CK(cudaMemcpyAsync(h->dark_d, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
+  } else {
+    CK(cudaMemcpyAsync(tmp, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
+    CK(epie::launch_dark_ingest(tmp, h->dark_d, h->cfg.N, h->st));
+    h->launches_total += 1;
+  }
   CK(cudaStreamSynchronize(h->st));
   h->has_dark = true;
   return EPIE_OK;
@@ -778,24 +783,30 @@ static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t
     else
       cudaGetLastError();
   }
+  // frames already in FFT order go straight to the frame set; DC-centred
+  // frames pass through the staging buffer and the re-layout kernel
+  const bool fft_order = (h->cfg.flags & EPIE_FRAMES_FFT_ORDER) != 0;
   for (int32_t a = 0; a < n; a += per) {
     const int m = std::min(per, n - a);
     const char *src = static_cast<const char *>(frames) + fb * static_cast<size_t>(a);
+    char *dst = dst0 + fb * static_cast<size_t>(a);
+    char *to = fft_order ? dst : static_cast<char *>(h->stage_d);
     if (device || pinned) {
-      // device or page-locked source: one copy into the device staging buffer
-      CK(cudaMemcpyAsync(h->stage_d, src, fb * m,
+      // device or page-locked source: one copy
+      CK(cudaMemcpyAsync(to, src, fb * m,
                          device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->up));
     } else {
       const int b = h->stage_next;
       h->stage_next ^= 1;
       CK(cudaEventSynchronize(h->ev_stage[b]));  // buffer b free again
       std::memcpy(h->stage_h[b], src, fb * m);
-      CK(cudaMemcpyAsync(h->stage_d, h->stage_h[b], fb * m, cudaMemcpyHostToDevice, h->up));
+      CK(cudaMemcpyAsync(to, h->stage_h[b], fb * m, cudaMemcpyHostToDevice, h->up));
       CK(cudaEventRecord(h->ev_stage[b], h->up));
     }
-    CK(epie::launch_ingest(h->stage_d, dst0 + fb * static_cast<size_t>(a), m, N,
-                           static_cast<int>(es), h->up));
-    h->launches_total += 1;
+    if (!fft_order) {
+      CK(epie::launch_ingest(h->stage_d, dst, m, N, static_cast<int>(es), h->up));
+      h->launches_total += 1;
+    }
   }
   CK(cudaMemcpyAsync(h->pos_d + 2 * static_cast<size_t>(h->n_frames), pos,
                      sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, h->up));

@@ -373,7 +373,7 @@ cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, in
                                 unsigned long long *pmax2_next, cudaStream_t st) {
   const int K = N * N;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid_for(K, 64, 152 * 4), 1, 1);
+  cfg.gridDim = dim3(grid_for(K, 64, 152 * 8), 1, 1);
   cfg.blockDim = dim3(256, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -390,7 +390,7 @@ cudaError_t launch_probe_reduce_table(float2 *P, const float2 *part, const int32
                                       cudaStream_t st) {
   const int K = N * N;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid_for(K, 64, 152 * 4), 1, 1);
+  cfg.gridDim = dim3(grid_for(K, 64, 152 * 8), 1, 1);
   cfg.blockDim = dim3(256, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

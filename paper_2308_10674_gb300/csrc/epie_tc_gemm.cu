@@ -139,7 +139,13 @@ struct TcCfg {
   // full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then the TMEM
   // address slot and the abort word
   static constexpr int NBAR = 2 * TC_STAGES + 5;
-  static constexpr size_t SMEM = 1024 + OFF_BAR + 8 * NBAR + 16;
+  // per epilogue warp a 32 x 32 fp32 staging tile, rows padded to 36 floats
+  // (16-byte aligned rows; 8 lanes of a quarter-warp touch distinct banks)
+  static constexpr int STG_PITCH = 36;
+  static constexpr size_t OFF_STG = (OFF_BAR + 8 * NBAR + 16 + 15) / 16 * 16;
+  static constexpr size_t STG_BYTES = 32 * STG_PITCH * 4;
+  static constexpr size_t SMEM = 1024 + OFF_STG + 4 * STG_BYTES;
+  static_assert(OFF_STG % 16 == 0, "staging tiles are read as float4");
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms stay aligned");
 };
 
@@ -274,17 +280,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_after();
       const int m0 = (tile / n_tiles) * TC_BM, n0 = (tile % n_tiles) * BN;
-      float *drow = D + static_cast<size_t>(m0 + 32 * q + lane) * ldd + n0;
       const uint32_t tq = tmem + static_cast<uint32_t>(b * BN) + (static_cast<uint32_t>(32 * q) << 16);
+      // lane l holds row l of the warp's 32 rows; through the staging tile,
+      // lanes 8i..8i+7 then store 128 contiguous bytes of one row
+      float *stg = reinterpret_cast<float *>(smem + C::OFF_STG + (warp - 2) * C::STG_BYTES);
+      const int sr = lane >> 3, sc = (lane & 7) * 4;
+      float *dbase = D + static_cast<size_t>(m0 + 32 * q) * ldd + n0;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
         tmem_ld32(tq + c, r);
 #pragma unroll
         for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<float4 *>(drow + c + j) =
+          *reinterpret_cast<float4 *>(stg + lane * C::STG_PITCH + j) =
               make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = 4 * i + sr;
+          *reinterpret_cast<float4 *>(dbase + static_cast<size_t>(row) * ldd + c + sc) =
+              *reinterpret_cast<const float4 *>(stg + row * C::STG_PITCH + sc);
+        }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();

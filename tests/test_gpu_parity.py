@@ -398,3 +398,24 @@ def test_append_from_device_tensor(orc):
         B.epie_append_frames_device(eng.h, t.data_ptr(), d["pos"], len(d["pos"]))
         e_g = eng.iterate(1)
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+
+
+def test_frames_in_fft_order_flag():
+    """EPIE_FRAMES_FFT_ORDER: frames and dark field given with the zero
+    frequency at [0,0] are stored as given, and the run is bit-identical to
+    the DC-centred input re-laid out by the engine."""
+    d = synth.small_scan(128, 3, 4, 65, seed=12)
+    rng = np.random.default_rng(4)
+    dark = (20.0 * rng.random((128, 128))).astype(np.float32)
+    fr_fft = np.ascontiguousarray(np.fft.ifftshift(d["frames"], axes=(-2, -1)))
+    dark_fft = np.ascontiguousarray(np.fft.ifftshift(dark))
+    outs = []
+    for frames, dk, flags in [(d["frames"], dark, 0), (fr_fft, dark_fft, B.EPIE_FRAMES_FFT_ORDER)]:
+        with engine(d, B.EPIE_COLOURED, flat_start(d), flags=flags) as eng:
+            eng.set_dark(dk)
+            eng.append(frames[:5], d["pos"][:5])
+            eng.append(frames[5:], d["pos"][5:])
+            e = eng.iterate(2)
+            outs.append((eng.object(), eng.probe(), e))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
