@@ -690,7 +690,25 @@ def run_tc_gemm(args):
             ms = timed(lambda: torch.matmul(A0, B0.t()), args.steps * 2)
             rows.append({"shape": [M, Nn, K], "what": what, "cublas_bf16_ms": ms,
                          "tflops": 2.0 * M * Nn * K / ms / 1e9})
-            del A0, A1, B0, B1, D
+            del A0, A1, B0, B1
+            if what != "square":  # fp32 operands read as tf32 (kind::tf32)
+                F = [torch.randn(r, K, device=dev, generator=g) for r in (M, M, Nn, Nn)]
+                for terms in (1, 3):
+                    f = lambda: B.epie_tc_gemm_tf32(F[0].data_ptr(), F[1].data_ptr(),
+                                                    F[2].data_ptr(), F[3].data_ptr(),
+                                                    D.data_ptr(), M, Nn, K, Nn, terms,
+                                                    status.data_ptr(), st)
+                    ms = timed(f, args.steps * 2)
+                    launches += args.steps * 2
+                    if int(status.item()):
+                        raise RuntimeError("tcgen05 GEMM reported a wait time-out")
+                    nbytes = M * K * 4 * (2 if terms == 3 else 1) + Nn * K * 4 * 2 + M * Nn * 4
+                    rows.append({"shape": [M, Nn, K], "what": what, "operands": "tf32",
+                                 "terms": terms, "ms": ms,
+                                 "tflops": 2.0 * M * Nn * K * terms / ms / 1e9,
+                                 "hbm_gbs": nbytes / ms / 1e6})
+                del F
+            del D
             torch.cuda.empty_cache()
     head = rows[1]  # 256^2 DFT rows, three terms
     M, Nn, K = head["shape"]

@@ -114,6 +114,10 @@ typedef struct epie_ctx *epie_t;
 #define EPIE_GEMM_TC_BF16 4  /* bf16 operands, this library's tcgen05 kernel     */
 #define EPIE_GEMM_TC_BF16X3 5 /* split bf16, this library's tcgen05 kernel: the
                                 three products share one TMEM accumulator       */
+#define EPIE_GEMM_TC_TF32 6  /* fp32 operands read as tf32, own tcgen05 kernel  */
+#define EPIE_GEMM_TC_TF32X3 7 /* split tf32 (x = hi + lo, hi = x with its low 13
+                                mantissa bits cleared): hi*hi + hi*lo + lo*hi in
+                                one TMEM accumulator, own tcgen05 kernel        */
 
 /* flags */
 #define EPIE_CHECKED 1u      /* keep O, P of the sweep start; restore them when
@@ -348,6 +352,15 @@ EPIE_API int epie_frames_to_fft_order(const void *src, void *dst, int32_t n, int
 EPIE_API int epie_tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1,
                                float *D, int64_t M, int32_t Nn, int32_t K, int32_t ldd,
                                int32_t terms, int32_t *status, void *stream);
+
+/* The same product with fp32 operands that the tensor cores read as tf32
+ * (tcgen05 kind::tf32: sign, exponent and the top 10 mantissa bits).  With
+ * terms = 3 and each operand split as x = hi + lo, both tf32-exact, the sum
+ * carries about 21 significant bits.  K % 32 == 0; otherwise as
+ * epie_tc_gemm_bf16. */
+EPIE_API int epie_tc_gemm_tf32(const float *A0, const float *A1, const float *B0,
+                               const float *B1, float *D, int64_t M, int32_t Nn, int32_t K,
+                               int32_t ldd, int32_t terms, int32_t *status, void *stream);
 
 /* FP32 FMA throughput of `device`: a kernel of independent FMA chains on
  * every SM (8 blocks of 256 threads per SM, `iters` x 256 FMAs per thread,

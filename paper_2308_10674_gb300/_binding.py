@@ -21,7 +21,7 @@ EPIE_SEQUENTIAL, EPIE_COLOURED, EPIE_MINIBATCH = 0, 1, 2
 EPIE_OMAX_PATCH, EPIE_OMAX_GLOBAL = 0, 1
 EPIE_PATH_FUSED, EPIE_PATH_PLAIN, EPIE_PATH_GEMM = 0, 1, 2
 EPIE_GEMM_BF16, EPIE_GEMM_TF32, EPIE_GEMM_BF16X3, EPIE_GEMM_FP32EMU = 0, 1, 2, 3
-EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3 = 4, 5
+EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3, EPIE_GEMM_TC_TF32, EPIE_GEMM_TC_TF32X3 = 4, 5, 6, 7
 EPIE_CHECKED, EPIE_PROBE_SUM, EPIE_GRAPH, EPIE_FRAMES_FFT_ORDER = 1, 2, 4, 8
 
 STATUS = {0: "EPIE_OK", -1: "EPIE_EINVAL", -2: "EPIE_ERANGE", -3: "EPIE_ECAPACITY",
@@ -94,6 +94,7 @@ def lib():
         L.epie_amp_loss_grad.argtypes = [C.POINTER(epie_amp_grad_args), C.POINTER(C.c_double)]
         L.epie_frames_to_fft_order.argtypes = [vp, vp, i32, i32, i32, vp]
         L.epie_tc_gemm_bf16.argtypes = [vp, vp, vp, vp, vp, C.c_int64, i32, i32, i32, i32, vp, vp]
+        L.epie_tc_gemm_tf32.argtypes = [vp, vp, vp, vp, vp, C.c_int64, i32, i32, i32, i32, vp, vp]
         L.epie_fp32_fma_peak.argtypes = [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.epie_error.argtypes = [H]
         L.epie_error.restype = C.c_char_p
@@ -322,6 +323,16 @@ def epie_fp32_fma_peak(device=0, iters=4096):
     if rc != EPIE_OK:
         raise EpieError(rc, epie_error(None))
     return t.value, m.value
+
+
+def epie_tc_gemm_tf32(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status, stream=None):
+    """D = sum_t A_t B_t^T with fp32 operands read as tf32 (integer device
+    addresses, as epie_tc_gemm_bf16)."""
+    v = lambda x: C.c_void_p(x) if x else None
+    rc = lib().epie_tc_gemm_tf32(v(A0), v(A1), v(B0), v(B1), v(D), M, Nn, K, ldd, terms,
+                                 v(status), v(stream))
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(None))
 
 
 def epie_amp_grad_scratch_bytes(N, n):

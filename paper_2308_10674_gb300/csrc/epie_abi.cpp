@@ -596,7 +596,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.mode == EPIE_MINIBATCH && c.batch < 1) why = "batch must be >= 1";
   else if (c.omax_mode != EPIE_OMAX_PATCH && c.omax_mode != EPIE_OMAX_GLOBAL) why = "bad omax_mode";
   else if (c.path < EPIE_PATH_FUSED || c.path > EPIE_PATH_GEMM) why = "bad path";
-  else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_TC_BF16X3)
+  else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_TC_TF32X3)
     why = "bad gemm_precision";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
   else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH | EPIE_FRAMES_FFT_ORDER))
@@ -1157,6 +1157,16 @@ int epie_tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void
   const int rc = epie::tc_gemm_bf16(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status,
                                     static_cast<cudaStream_t>(stream), &why);
   if (rc) g_init_error = "epie_tc_gemm_bf16: " + why;
+  return rc;
+}
+
+int epie_tc_gemm_tf32(const float *A0, const float *A1, const float *B0, const float *B1,
+                      float *D, int64_t M, int32_t Nn, int32_t K, int32_t ldd, int32_t terms,
+                      int32_t *status, void *stream) {
+  std::string why;
+  const int rc = epie::tc_gemm_tf32(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status,
+                                    static_cast<cudaStream_t>(stream), &why);
+  if (rc) g_init_error = "epie_tc_gemm_tf32: " + why;
   return rc;
 }
 

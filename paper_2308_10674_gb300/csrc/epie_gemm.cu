@@ -20,12 +20,16 @@
 //   EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3: the bf16 and split-bf16 products
 //     on this engine's own tcgen05 kernel (epie_tc_gemm.cu), the three
 //     split products accumulated in one tensor-memory accumulator
+//   EPIE_GEMM_TC_TF32, EPIE_GEMM_TC_TF32X3: the same kernel on fp32 operands
+//     read as tf32 (kind::tf32); the split form takes hi = x with its low 13
+//     mantissa bits cleared and lo = x - hi, both tf32-exact
 // Twiddles are evaluated in double precision on the host (exact k j mod N).
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -42,6 +46,9 @@ struct GemmPath {
   __nv_bfloat16 *Tf_hi = nullptr, *Tf_lo = nullptr, *Ti_hi = nullptr, *Ti_lo = nullptr;
   // transposed twiddles (K-major B operand of the tcgen05 kernel)
   __nv_bfloat16 *Tft_hi = nullptr, *Tft_lo = nullptr, *Tit_hi = nullptr, *Tit_lo = nullptr;
+  // transposed twiddles split for the tf32 kernel (fp32 hi / lo)
+  float *Tft32_hi = nullptr, *Tft32_lo = nullptr, *Tit32_hi = nullptr, *Tit32_lo = nullptr;
+  float *F_hi = nullptr, *F_lo = nullptr;                   // tf32 split rows, cap * N * 2N
   float2 *psi = nullptr, *Y = nullptr;                      // cap * N * N complex each
   __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;           // cap * N * 2N
   double *omax = nullptr;                                   // cap
@@ -123,6 +130,19 @@ __global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt) {
   }
 }
 
+// x = hi + lo with hi = x without its low 13 mantissa bits (tf32-exact) and
+// lo = x - hi, exact in fp32 and itself tf32-exact
+__global__ void split_tf32_kernel(const float *__restrict__ x, float *__restrict__ hi,
+                                  float *__restrict__ lo, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float v = x[i];
+    const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    hi[i] = h;
+    lo[i] = v - h;
+  }
+}
+
 int grid_for(long long n, int nt, int cap) {
   long long g = (n + nt - 1) / nt;
   if (g > cap) g = cap;
@@ -135,9 +155,21 @@ cudaError_t split(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long lon
   return cudaGetLastError();
 }
 
-bool tc_precision(int p) { return p == EPIE_GEMM_TC_BF16 || p == EPIE_GEMM_TC_BF16X3; }
-bool split_precision(int p) { return p == EPIE_GEMM_BF16 || p == EPIE_GEMM_BF16X3 || tc_precision(p); }
+bool tc_bf16_precision(int p) { return p == EPIE_GEMM_TC_BF16 || p == EPIE_GEMM_TC_BF16X3; }
+bool tc_tf32_precision(int p) { return p == EPIE_GEMM_TC_TF32 || p == EPIE_GEMM_TC_TF32X3; }
+bool tc_precision(int p) { return tc_bf16_precision(p) || tc_tf32_precision(p); }
+bool split_precision(int p) {
+  return p == EPIE_GEMM_BF16 || p == EPIE_GEMM_BF16X3 || tc_bf16_precision(p);
+}
 bool x3_precision(int p) { return p == EPIE_GEMM_BF16X3 || p == EPIE_GEMM_TC_BF16X3; }
+
+float tf32_hi(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  u &= 0xFFFFE000u;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
 
 // dst (rows x 2N fp32) = src (rows x 2N) * T, T the 2N x 2N twiddle matrix
 int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool inverse,
@@ -148,17 +180,32 @@ int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool i
   cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
   const float *srcf = reinterpret_cast<const float *>(src);
   float *dstf = reinterpret_cast<float *>(dst);
-  if (tc_precision(g->precision)) {
+  // the kernel takes rows in blocks of 128; the buffers hold an even number
+  // of frames, so the rows past the group (N = 64, odd group) exist and
+  // their results are never read
+  const long long mrows = (rows + 127) / 128 * 128;
+  if (g->precision == EPIE_GEMM_TC_TF32)
+    return tc_gemm_tf32(srcf, nullptr, inverse ? g->Ti : g->Tf, nullptr, dstf, mrows, n2, n2, n2,
+                        1, err_flag, st, err);
+  if (g->precision == EPIE_GEMM_TC_TF32X3) {
+    split_tf32_kernel<<<grid_for(rows * n2, 256, 152 * 16), 256, 0, st>>>(srcf, g->F_hi, g->F_lo,
+                                                                           rows * n2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return EPIE_ECUDA;
+    }
+    return tc_gemm_tf32(g->F_hi, g->F_lo, inverse ? g->Tit32_hi : g->Tft32_hi,
+                        inverse ? g->Tit32_lo : g->Tft32_lo, dstf, mrows, n2, n2, n2, 3, err_flag,
+                        st, err);
+  }
+  if (tc_bf16_precision(g->precision)) {
     const bool x3 = g->precision == EPIE_GEMM_TC_BF16X3;
     cudaError_t e = split(srcf, g->D_hi, x3 ? g->D_lo : nullptr, rows * n2, st);
     if (e != cudaSuccess) {
       *err = cudaGetErrorString(e);
       return EPIE_ECUDA;
     }
-    // the kernel takes rows in blocks of 128; the buffers hold an even number
-    // of frames, so the rows past the group (N = 64, odd group) exist and
-    // their results are never read
-    const long long mrows = (rows + 127) / 128 * 128;
     return tc_gemm_bf16(g->D_hi, x3 ? g->D_lo : nullptr, inverse ? g->Tit_hi : g->Tft_hi,
                         x3 ? (inverse ? g->Tit_lo : g->Tft_lo) : nullptr, dstf, mrows, n2, n2, n2,
                         x3 ? 3 : 1, err_flag, st, err);
@@ -216,7 +263,8 @@ void gemm_path_destroy(GemmPath *g) {
   if (g->blas) cublasDestroy(g->blas);
   void *ptrs[] = {g->Tf,     g->Ti,     g->Tf_hi,  g->Tf_lo, g->Ti_hi, g->Ti_lo,
                   g->Tft_hi, g->Tft_lo, g->Tit_hi, g->Tit_lo, g->psi,   g->Y,
-                  g->D_hi,   g->D_lo,   g->omax};
+                  g->D_hi,   g->D_lo,   g->omax,   g->Tft32_hi, g->Tft32_lo, g->Tit32_hi,
+                  g->Tit32_lo, g->F_hi, g->F_lo};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -269,6 +317,21 @@ GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *e
          split(g->Tf, g->Tft_hi, g->Tft_lo, static_cast<long long>(Tf.size()), st) == cudaSuccess &&
          split(g->Ti, g->Tit_hi, g->Tit_lo, static_cast<long long>(Ti.size()), st) == cudaSuccess &&
          cudaStreamSynchronize(st) == cudaSuccess;
+    if (ok && precision == EPIE_GEMM_TC_TF32X3) {
+      std::vector<float> fh(Tft.size()), fl(Tft.size()), ih(Tit.size()), il(Tit.size());
+      for (size_t i = 0; i < Tft.size(); ++i) {
+        fh[i] = tf32_hi(Tft[i]);
+        fl[i] = Tft[i] - fh[i];
+        ih[i] = tf32_hi(Tit[i]);
+        il[i] = Tit[i] - ih[i];
+      }
+      ok = cudaMalloc(&g->Tft32_hi, tb) == cudaSuccess && cudaMalloc(&g->Tft32_lo, tb) == cudaSuccess &&
+           cudaMalloc(&g->Tit32_hi, tb) == cudaSuccess && cudaMalloc(&g->Tit32_lo, tb) == cudaSuccess;
+      ok = ok && cudaMemcpy(g->Tft32_hi, fh.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(g->Tft32_lo, fl.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(g->Tit32_hi, ih.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(g->Tit32_lo, il.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
   }
   if (!ok) {
     *err = "GEMM path: twiddle matrices could not be set up";
@@ -282,11 +345,12 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
   if (members <= g->cap) return EPIE_OK;
   int cap = members > 2 * g->cap ? members : 2 * g->cap;
   cap += cap & 1;  // even: whole 128-row blocks at N = 64
-  void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax};
+  void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax, g->F_hi, g->F_lo};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->psi = g->Y = nullptr;
   g->D_hi = g->D_lo = nullptr;
+  g->F_hi = g->F_lo = nullptr;
   g->omax = nullptr;
   g->cap = 0;
   const size_t K = static_cast<size_t>(g->N) * g->N;
@@ -298,6 +362,9 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
     if (ok && x3_precision(g->precision))
       ok = cudaMalloc(&g->D_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
   }
+  if (ok && g->precision == EPIE_GEMM_TC_TF32X3)
+    ok = cudaMalloc(&g->F_hi, sizeof(float) * 2 * K * cap) == cudaSuccess &&
+         cudaMalloc(&g->F_lo, sizeof(float) * 2 * K * cap) == cudaSuccess;
   if (!ok) {
     *err = "GEMM path: out of device memory for a group of " + std::to_string(cap);
     return EPIE_ECUDA;
@@ -337,8 +404,9 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
-  const bool split_launch = split_precision(g->precision);
-  *kernels += 5 + (split_launch ? 4 : 0);  // gather, 2 transposes, modulus, update (+ splits)
+  const bool split_launch = split_precision(g->precision) || g->precision == EPIE_GEMM_TC_TF32X3;
+  // gather, 2 transposes, modulus, update (+ 4 splits, + 4 tcgen05 GEMMs)
+  *kernels += 5 + (split_launch ? 4 : 0) + (tc_precision(g->precision) ? 4 : 0);
   return EPIE_OK;
 }
 

@@ -120,6 +120,10 @@ cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, floa
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err);
+// the same with fp32 operands read as tf32 (kind::tf32); K a multiple of 32
+int tc_gemm_tf32(const float *A0, const float *A1, const float *B0, const float *B1, float *D,
+                 long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
+                 std::string *err);
 
 // FP32 FMA-chain throughput (epie_peak.cu)
 int fma_peak(int device, int iters, double *tflops, double *sm_mhz, std::string *err);

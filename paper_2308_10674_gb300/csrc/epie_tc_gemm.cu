@@ -2,28 +2,34 @@
 //
 //   D[M x Nn] (fp32, row pitch ldd) = sum over terms t of A_t[M x K] * B_t[Nn x K]^T
 //
-// A_t and B_t are bf16, row-major with K contiguous (both operands K-major).
-// One term is the plain bf16 product (A0 B0); three terms are the split-bf16
-// product A0 B0 + A0 B1 + A1 B0 (x = x_hi + x_lo), all accumulated in one
-// fp32 accumulator in tensor memory.  In the DFT path A is a block of rows of
+// A_t and B_t are bf16 (kind::f16) or fp32 read as tf32 (kind::tf32),
+// row-major with K contiguous (both operands K-major).  One term is the plain
+// product (A0 B0); three terms are the split product A0 B0 + A0 B1 + A1 B0
+// (x = x_hi + x_lo), all accumulated in one fp32 accumulator in tensor
+// memory.  In the DFT path A is a block of rows of
 // interleaved complex values and B the transposed 2N x 2N twiddle matrix, so
 // one call is the DFT of every row (Sec. "ePIE Implementation": the
 // projection runs through a DFT of 2^n frames).
 //
-// Kernel design (one CTA = one 128 x BN tile of D, 128 threads):
-//   * operand tiles 128 x 64 (A) and BN x 64 (B) bf16 are fetched by TMA
-//     (cp.async.bulk.tensor.2d, 128-byte swizzle) into a 4-stage ring in
-//     shared memory; mbarrier "full[s]" completes on the copied bytes;
+// Kernel design (persistent, one CTA of 192 threads per SM; 128 x BN tiles
+// of D, BN = 256, or 128 when Nn is not a multiple of 256):
+//   * operand tiles of 128 (A) and BN (B) rows of 128 bytes (64 bf16 or 32
+//     fp32 values of K) are fetched by TMA (cp.async.bulk.tensor.2d,
+//     128-byte swizzle) into a 4-stage ring in shared memory; mbarrier
+//     "full[s]" completes on the copied bytes;
 //   * thread 0 of warp 0 issues the copies; thread 0 of warp 1 issues
-//     tcgen05.mma (M = 128, N = BN, K = 16, kind::f16, bf16 x bf16 -> fp32)
-//     from shared-memory descriptors into a BN-column TMEM accumulator, and
-//     tcgen05.commit on "empty[s]" returns the stage to the producer;
-//   * after the last k-block a final commit completes "done"; each warp then
-//     reads its 32 accumulator rows (TMEM lanes 32w..32w+31) with
-//     tcgen05.ld.32x32b and stores them as 16-byte vectors.
+//     tcgen05.mma (M = 128, N = BN, 32 bytes of the rows per instruction:
+//     kind::f16 with bf16 or kind::tf32; fp32 accumulation) from
+//     shared-memory descriptors, and tcgen05.commit on "empty[s]" returns
+//     the stage to the producer;
+//   * two BN-column accumulators alternate in tensor memory; after a tile's
+//     last k-block a commit completes "acc_full[b]", warps 2-5 read the rows
+//     of their TMEM lane quadrant with tcgen05.ld.32x32b, stage them through
+//     shared memory and store whole 128-byte row segments, then arrive on
+//     "acc_empty[b]", while the MMAs of the next tile run.
 // Every wait is bounded by %globaltimer (2 s).  On expiry the kernel sets
-// FLAG_TC_TIMEOUT in the status word, skips the epilogue, lets its issued
-// copies land (bounded again), frees its tensor memory and returns.
+// FLAG_TC_TIMEOUT in the status word, stops, lets its issued copies land and
+// its MMAs finish (bounded again), frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -39,7 +45,14 @@ namespace epie {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_STAGES = 4;
+// every operand row of a stage is 128 bytes (one swizzle width): 64 bf16 or
+// 32 fp32/tf32 values of K
+template <bool TF32>
+struct TcElem {
+  static constexpr int BYTES = TF32 ? 4 : 2;
+  static constexpr int BK = 128 / BYTES;
+};
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -83,23 +96,33 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
          (static_cast<uint64_t>(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16: fp32 accumulator [4,6) = 1, A and B
-// bf16 [7,10) = [10,13) = 1, both K-major (bits 15, 16 clear), N >> 3 at
-// [17,23), M >> 4 at [24,29).
-template <int M, int N>
-__host__ __device__ constexpr uint32_t f16_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
+// Instruction descriptor: fp32 accumulator [4,6) = 1; A and B format at
+// [7,10) and [10,13): bf16 = 1 under kind::f16, tf32 = 2 under kind::tf32;
+// both K-major (bits 15, 16 clear); N >> 3 at [17,23), M >> 4 at [24,29).
+template <int M, int N, bool TF32>
+__host__ __device__ constexpr uint32_t mma_idesc() {
+  return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+// one MMA over 32 bytes of the operand rows (16 bf16 or 8 tf32 values of K)
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accumulate) {
+  if constexpr (TF32)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile(
@@ -132,8 +155,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 template <int BN>
 struct TcCfg {
-  static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
-  static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
+  static constexpr uint32_t A_BYTES = TC_BM * 128;
+  static constexpr uint32_t B_BYTES = BN * 128;
   static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
   static constexpr size_t OFF_BAR = static_cast<size_t>(TC_STAGES) * STAGE;
   // full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then the TMEM
@@ -155,7 +178,7 @@ constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA (owns TMEM), warps 2-
 // t / n_tiles, column block t % n_tiles, so neighbouring CTAs share the row
 // block in L2).  Two accumulators of BN columns alternate in TMEM: the
 // epilogue drains tile i while the MMAs of tile i + 1 run.
-template <int BN>
+template <int BN, bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
@@ -174,7 +197,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int *abort_word = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kb_term = K / TC_BK, nkb = kb_term * terms;
+  constexpr int BK = TcElem<TF32>::BK;
+  const int kb_term = K / BK, nkb = kb_term * terms;
   const int tiles = m_tiles * n_tiles;
   auto fail = [&]() {
     *abort_word = 1;
@@ -213,7 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           if (*abort_word) break;
-          const int t = kb / kb_term, kx = (kb % kb_term) * TC_BK;
+          const int t = kb / kb_term, kx = (kb % kb_term) * BK;
           const CUtensorMap *ma = t == 2 ? &mA1 : &mA0;  // terms: A0 B0, A0 B1, A1 B0
           const CUtensorMap *mb = t == 1 ? &mB1 : &mB0;
           uint8_t *sa = smem + static_cast<size_t>(s) * C::STAGE;
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      constexpr uint32_t idesc = f16_idesc<TC_BM, BN>();
+      constexpr uint32_t idesc = mma_idesc<TC_BM, BN, TF32>();
       int it = 0, tl = 0;
       for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
         if (*abort_word) break;
@@ -253,9 +277,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t a_addr = smem_u32(smem + static_cast<size_t>(s) * C::STAGE);
           const uint32_t b_addr = a_addr + C::A_BYTES;
 #pragma unroll
-          for (int k = 0; k < TC_BK / 16; ++k)  // K = 16 per instruction: 32 bytes along the row
-            umma_f16(acc, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
-                     idesc, (kb | k) != 0);
+          for (int k = 0; k < 4; ++k)  // 32 bytes of the 128-byte rows per instruction
+            umma<TF32>(acc, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
+                       idesc, (kb | k) != 0);
           umma_commit(&empty[s]);
         }
         if (bad) break;
@@ -340,17 +364,20 @@ EncodeTiled encoder(std::string *err) {
   return fn;
 }
 
-// rows x K bf16, row-major; box = box_rows x 64, 128-byte swizzle
-bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_rows,
+// rows x K values (bf16, or fp32 read as tf32), row-major; box = box_rows x
+// (128 bytes of K), 128-byte swizzle
+bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_rows, bool tf32,
               std::string *err) {
   EncodeTiled enc = encoder(err);
   if (!enc) return false;
+  const int es = tf32 ? 4 : 2;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * es};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / es), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = enc(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     *err = "cuTensorMapEncodeTiled failed (" + std::to_string(static_cast<int>(r)) + ")";
@@ -359,7 +386,7 @@ bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_r
   return true;
 }
 
-template <int BN>
+template <int BN, bool TF32>
 cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                       const CUtensorMap &b1, float *D, long long M, int Nn, int K, int ldd,
                       int terms, int *err_flag, cudaStream_t st) {
@@ -368,7 +395,7 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(C::SMEM));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -378,9 +405,50 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
   const int m_tiles = static_cast<int>(M / TC_BM), n_tiles = Nn / BN;
   const long long tiles = static_cast<long long>(m_tiles) * n_tiles;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);  // one CTA per SM
-  tc_gemm_kernel<BN><<<grid, TC_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms, m_tiles,
-                                                          n_tiles, err_flag);
+  tc_gemm_kernel<BN, TF32><<<grid, TC_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms,
+                                                                m_tiles, n_tiles, err_flag);
   return cudaGetLastError();
+}
+
+int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, float *D, long long M,
+            int Nn, int K, int ldd, int terms, bool tf32, int *err_flag, cudaStream_t st,
+            std::string *err) {
+  const int BN = Nn % 256 == 0 ? 256 : 128;
+  const int bk = tf32 ? TcElem<true>::BK : TcElem<false>::BK;
+  if (!A0 || !B0 || !D || !err_flag || (terms != 1 && terms != 3) ||
+      (terms == 3 && (!A1 || !B1))) {
+    *err = "null operand, or terms not 1 or 3";
+    return EPIE_EINVAL;
+  }
+  if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % bk || ldd < Nn || ldd % 4 ||
+      (M / TC_BM) * (Nn / 128) > 0x7fffffffLL) {
+    *err = "M must be a positive multiple of 128, Nn of 128, K of " + std::to_string(bk) +
+           "; ldd >= Nn and a multiple of 4";
+    return EPIE_EINVAL;
+  }
+  const void *ptrs[5] = {A0, A1 ? A1 : A0, B0, B1 ? B1 : B0, D};
+  for (const void *p : ptrs)
+    if (reinterpret_cast<uintptr_t>(p) % 16) {
+      *err = "operands must be 16-byte aligned";
+      return EPIE_EINVAL;
+    }
+  CUtensorMap a0, a1, b0, b1;
+  if (!make_map(&a0, A0, M, K, TC_BM, tf32, err) ||
+      !make_map(&a1, A1 ? A1 : A0, M, K, TC_BM, tf32, err) ||
+      !make_map(&b0, B0, Nn, K, BN, tf32, err) || !make_map(&b1, B1 ? B1 : B0, Nn, K, BN, tf32, err))
+    return EPIE_ECUDA;
+  cudaError_t e;
+  if (tf32)
+    e = BN == 256 ? launch_tc<256, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
+                  : launch_tc<128, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
+  else
+    e = BN == 256 ? launch_tc<256, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
+                  : launch_tc<128, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  return EPIE_OK;
 }
 
 }  // namespace
@@ -388,35 +456,13 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err) {
-  const int BN = Nn % 256 == 0 ? 256 : 128;
-  if (!A0 || !B0 || !D || !err_flag || (terms != 1 && terms != 3) ||
-      (terms == 3 && (!A1 || !B1))) {
-    *err = "tc_gemm_bf16: null operand, or terms not 1 or 3";
-    return EPIE_EINVAL;
-  }
-  if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % TC_BK || ldd < Nn ||
-      ldd % 4 || (M / TC_BM) * (Nn / 128) > 0x7fffffffLL) {
-    *err = "tc_gemm_bf16: M must be a positive multiple of 128, Nn of 128, K of 64, "
-           "ldd >= Nn and a multiple of 4";
-    return EPIE_EINVAL;
-  }
-  const void *ptrs[5] = {A0, A1 ? A1 : A0, B0, B1 ? B1 : B0, D};
-  for (const void *p : ptrs)
-    if (reinterpret_cast<uintptr_t>(p) % 16) {
-      *err = "tc_gemm_bf16: operands must be 16-byte aligned";
-      return EPIE_EINVAL;
-    }
-  CUtensorMap a0, a1, b0, b1;
-  if (!make_map(&a0, A0, M, K, TC_BM, err) || !make_map(&a1, A1 ? A1 : A0, M, K, TC_BM, err) ||
-      !make_map(&b0, B0, Nn, K, BN, err) || !make_map(&b1, B1 ? B1 : B0, Nn, K, BN, err))
-    return EPIE_ECUDA;
-  cudaError_t e = BN == 256 ? launch_tc<256>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
-                            : launch_tc<128>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
-  if (e != cudaSuccess) {
-    *err = cudaGetErrorString(e);
-    return EPIE_ECUDA;
-  }
-  return EPIE_OK;
+  return tc_gemm(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, false, err_flag, st, err);
+}
+
+int tc_gemm_tf32(const float *A0, const float *A1, const float *B0, const float *B1, float *D,
+                 long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
+                 std::string *err) {
+  return tc_gemm(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, true, err_flag, st, err);
 }
 
 }  // namespace epie

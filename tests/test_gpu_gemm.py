@@ -2,7 +2,8 @@
 coloured sweep from a well-conditioned textured start (tests/test_gpu_parity.py
 explains why).  Bounds per operand precision, from its unit roundoff u
 (bf16 2^-8, tf32 2^-11; the split bf16 product drops the lo*lo term, about
-2^-16; the fp32 emulation is fp32-accurate): relative L2 on object and probe
+2^-16, the split tf32 product about 2^-21; the fp32 emulation is
+fp32-accurate): relative L2 on object and probe
 and relative error of the sweep error metric within about 8u.  The TC_*
 precisions run the same products on the engine's own tcgen05 kernel; at
 N = 64 odd colour classes exercise its padded last row block."""
@@ -15,7 +16,8 @@ from paper_2308_10674_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {B.EPIE_GEMM_FP32EMU: 1e-5, B.EPIE_GEMM_BF16X3: 1e-4, B.EPIE_GEMM_TF32: 3e-3,
-          B.EPIE_GEMM_BF16: 3e-2, B.EPIE_GEMM_TC_BF16X3: 1e-4, B.EPIE_GEMM_TC_BF16: 3e-2}
+          B.EPIE_GEMM_BF16: 3e-2, B.EPIE_GEMM_TC_BF16X3: 1e-4, B.EPIE_GEMM_TC_BF16: 3e-2,
+          B.EPIE_GEMM_TC_TF32: 3e-3, B.EPIE_GEMM_TC_TF32X3: 1e-5}
 
 
 def rel(a, b):

@@ -1,5 +1,6 @@
-"""The hand-written tcgen05 GEMM (epie_tc_gemm_bf16) against exact FP64
-products of the same bf16 values, and, used as a row DFT, against numpy's FFT.
+"""The hand-written tcgen05 GEMM (epie_tc_gemm_bf16, and epie_tc_gemm_tf32 on
+fp32 operands read as tf32) against exact FP64 products of the same operand
+values, and, used as a row DFT, against numpy's FFT.
 
 D = sum_t A_t B_t^T with fp32 accumulation: every element must lie within
 4 K 2^-24 (|A| |B|^T) of the exact product (the fp32 summation bound with
@@ -33,15 +34,31 @@ def split(x):
     return hi, lo
 
 
-def run(A0, A1, B0, B1, M, Nn, K, ldd, terms):
+def tf32_hi(x):
+    """x with its low 13 mantissa bits cleared: tf32-exact."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return u.view(np.float32)
+
+
+def tf32_split(x):
+    x = np.ascontiguousarray(x, np.float32)
+    hi = tf32_hi(x)
+    return hi, (x - hi).astype(np.float32)
+
+
+def run(A0, A1, B0, B1, M, Nn, K, ldd, terms, tf32=False):
     dev = torch.device("cuda:0")
-    t = lambda a: None if a is None else torch.from_numpy(a.view(np.int16)).to(dev)
+    if tf32:
+        t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    else:
+        t = lambda a: None if a is None else torch.from_numpy(a.view(np.int16)).to(dev)
     tA0, tA1, tB0, tB1 = t(A0), t(A1), t(B0), t(B1)
     D = torch.full((M, ldd), float("nan"), dtype=torch.float32, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     ptr = lambda x: 0 if x is None else x.data_ptr()
-    B.epie_tc_gemm_bf16(ptr(tA0), ptr(tA1), ptr(tB0), ptr(tB1), D.data_ptr(), M, Nn, K, ldd,
-                        terms, status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    f = B.epie_tc_gemm_tf32 if tf32 else B.epie_tc_gemm_bf16
+    f(ptr(tA0), ptr(tA1), ptr(tB0), ptr(tB1), D.data_ptr(), M, Nn, K, ldd, terms,
+      status.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     D = D.cpu().numpy()
@@ -99,3 +116,52 @@ def test_tc_gemm_as_row_dft(N):
     got = D.reshape(rows, N, 2) @ np.array([1, 1j])
     ref = np.fft.fft(x.astype(np.complex128), axis=1)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-4
+
+
+@pytest.mark.parametrize("M,Nn,K,ldd,terms", [
+    (256, 256, 128, 256, 1),   # 4 k-blocks of 32
+    (384, 512, 256, 512, 3),   # 24 k-blocks through the ring, 2 column tiles
+    (128, 384, 96, 400, 1),    # 128-wide column tiles, row pitch > width
+])
+def test_tc_gemm_tf32_matches_exact_product(M, Nn, K, ldd, terms):
+    """kind::tf32 on tf32-exact operands (hi and lo of a split both are): the
+    result is the exact product up to fp32 summation."""
+    rng = np.random.default_rng(M + Nn + K + 1)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    Bm = rng.standard_normal((Nn, K)).astype(np.float32)
+    (A0, A1), (B0, B1) = tf32_split(A), tf32_split(Bm)
+    A1, B1 = tf32_hi(A1), tf32_hi(B1)  # lo made tf32-exact too
+    if terms == 1:
+        A1 = B1 = None
+    D = run(A0, A1, B0, B1, M, Nn, K, ldd, terms, tf32=True)
+    a0, b0 = A0.astype(np.float64), B0.astype(np.float64)
+    ref, absref = a0 @ b0.T, np.abs(a0) @ np.abs(b0).T
+    if terms == 3:
+        a1, b1 = A1.astype(np.float64), B1.astype(np.float64)
+        ref = ref + a0 @ b1.T + a1 @ b0.T
+        absref = absref + np.abs(a0) @ np.abs(b1).T + np.abs(a1) @ np.abs(b0).T
+    bound = 4 * K * terms * 2.0 ** -24 * absref + 1e-30
+    err = np.abs(D - ref)
+    assert np.all(err <= bound), (float(err.max()), float((err / bound).max()))
+    if terms == 3:  # about 21 significant bits of the fp32 inputs' product
+        exact = A.astype(np.float64) @ Bm.astype(np.float64).T
+        assert np.linalg.norm(D - exact) / np.linalg.norm(exact) < 1e-5
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_tc_gemm_tf32_as_row_dft(N):
+    """The split-tf32 product as a row DFT matches numpy's FFT to 1e-5."""
+    rows = 256
+    rng = np.random.default_rng(N + 7)
+    x = (rng.standard_normal((rows, N)) + 1j * rng.standard_normal((rows, N))).astype(np.complex64)
+    X = x.view(np.float32).reshape(rows, 2 * N)
+    k = np.arange(N)
+    F = np.exp(-2j * np.pi * np.outer(k, k) / N)
+    T = np.zeros((2 * N, 2 * N))
+    T[0::2, 0::2], T[1::2, 0::2] = F.real, -F.imag
+    T[0::2, 1::2], T[1::2, 1::2] = F.imag, F.real
+    (X0, X1), (T0, T1) = tf32_split(X), tf32_split(T.T.astype(np.float32))
+    D = run(X0, X1, T0, T1, rows, 2 * N, 2 * N, 2 * N, 3, tf32=True)
+    got = D.reshape(rows, N, 2) @ np.array([1, 1j])
+    ref = np.fft.fft(x.astype(np.complex128), axis=1)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
