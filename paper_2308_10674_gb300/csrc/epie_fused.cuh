@@ -62,7 +62,14 @@ struct FusedCfg {
   static constexpr size_t OFF_IRAW = OFF_I + IF_BYTES - I_BYTES;  // raw tile at the top
   static constexpr size_t OFF_RED = (OFF_I + IF_BYTES + 15) / 16 * 16;
   static constexpr size_t OFF_BAR = OFF_RED + sizeof(double) * (2 * NW + 2);
-  static constexpr size_t SMEM = OFF_BAR + 16;
+  static constexpr size_t SMEM = OFF_BAR + 16;  // mbarrier, then the TMEM address slot
+  // tensor memory: 64 columns per thread (32 for its object-patch values,
+  // 32 for its probe values) in its warp's lane quadrant
+  static constexpr int TM_COLS = (NW / 4) * 64;
+  static_assert(E == 16, "16 complex values per thread fill 32 TMEM columns");
+  static_assert(NW % 4 == 0 && (TM_COLS & (TM_COLS - 1)) == 0 && TM_COLS >= 32 &&
+                    TM_COLS <= 512,
+                "TMEM allocation is a power of two between 32 and 512 columns");
   static_assert(E * NT == N * WC, "tile must split evenly over threads");
   static_assert(I_BYTES % 16 == 0, "bulk copy size");
   static_assert(OFF_IRAW % 16 == 0, "bulk copy destination alignment");
@@ -135,13 +142,24 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
   const IT *frame = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * N * N;
 
+  // The object patch and probe values a thread reads in phase 1 are kept in
+  // tensor memory (unused otherwise by this kernel) until phase 3 needs them
+  // again, instead of being re-read from L2 / HBM.  Warp 0 allocates.
+  uint32_t *tm_slot = reinterpret_cast<uint32_t *>(smem + C::OFF_BAR + 8);
+  if (warp == 0) tmem_alloc(tm_slot, C::TM_COLS);
   // intensity rows [crank*HR, +HR) of the frame: one bulk copy, waited on
   // just before the modulus replacement
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tm_base = *tm_slot;
+  // this thread's columns: [0, 32) object patch, [32, 64) probe
+  const uint32_t tm = tm_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                      static_cast<uint32_t>((warp >> 2) * 64);
   if (tid == 0) {
     // the frame is read once per sweep: keep it from evicting the object
     mbar_arrive_expect_tx(bar, C::I_BYTES);
@@ -182,13 +200,17 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
         const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
         ov[i] = EPIE_LD_O(Obase + y * orow + xl);
       }
+      float keep[2 * EB];
 #pragma unroll
       for (int i = 0; i < EB; ++i) {
         const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
         const float q = ov[i].x * ov[i].x + ov[i].y * ov[i].y;
         if (q > om) { om = q; omv = ov[i]; }
         slab[ColA::at(xl, y)] = ov[i];
+        keep[2 * i] = ov[i].x;
+        keep[2 * i + 1] = ov[i].y;
       }
+      tmem_st16(tm + 2 * i0, keep);
     }
   };
   if (a.o_early) load_patch();
@@ -207,13 +229,18 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
       pv[i] = __ldg(Pbase + y * N + xl);
     }
+    float keep[2 * EB];
 #pragma unroll
     for (int i = 0; i < EB; ++i) {
       const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
       float2 &t = slab[ColA::at(xl, y)];  // written by this thread above
       t = cmul(pv[i], t);
+      keep[2 * i] = pv[i].x;
+      keep[2 * i + 1] = pv[i].y;
     }
+    tmem_st16(tm + 32 + 2 * i0, keep);
   }
+  tmem_wait_st();
   __syncthreads();
   EPIE_PHASE(1);
   fft_all<N, false, NT, WC, false, ColA>(slab, tw);
@@ -277,6 +304,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   // ---------------------------------------------------------------- phase 2
   bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
+  ok = __all_sync(0xffffffffu, ok);  // warp-uniform: phase 3 reads TMEM warp-collectively
   float isum_t = 0.f;  // sum I of this thread's tile elements
   {
     // intensity tile -> float max(I - dark, 0), in place: the raw tile sits
@@ -359,13 +387,16 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   if (ok && a.accO == nullptr) {
 #pragma unroll
     for (int i0 = 0; i0 < E; i0 += EB) {
-      // loads of a batch before its stores (the stores could alias them)
+      // the object patch and probe values kept in tensor memory in phase 1
+      float ko[2 * EB], kp[2 * EB];
+      tmem_ld16(tm + 2 * i0, ko);
+      tmem_ld16(tm + 32 + 2 * i0, kp);
+      tmem_wait_ld();
       float2 pv[EB], ov[EB];
 #pragma unroll
       for (int i = 0; i < EB; ++i) {
-        const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
-        pv[i] = __ldg(Pbase + y * N + xl);
-        ov[i] = EPIE_LD_O(Obase + y * orow + xl);
+        pv[i] = make_float2(kp[2 * i], kp[2 * i + 1]);
+        ov[i] = make_float2(ko[2 * i], ko[2 * i + 1]);
       }
 #pragma unroll
       for (int i = 0; i < EB; ++i) {
@@ -384,12 +415,18 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     // batch by the count-normalised sum, applied by a separate kernel
     const float inv_pm = pm > 0.0 ? static_cast<float>(1.0 / pm) : 0.f;
     const size_t obase = static_cast<size_t>(py) * orow + px + crank * WC;
+    float ko[2 * EB], kp[2 * EB];  // a batch of kept object / probe values
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int idx = tid + i * NT, y = idx / WC, xl = idx % WC;
+      if (i % EB == 0) {
+        tmem_ld16(tm + 2 * i, ko);
+        tmem_ld16(tm + 32 + 2 * i, kp);
+        tmem_wait_ld();
+      }
       const float2 psi1 = slab[ColA::at(xl, y)];
-      const float2 p = Pbase[y * N + xl];
-      const float2 o = Obase[y * orow + xl];
+      const float2 p = make_float2(kp[2 * (i % EB)], kp[2 * (i % EB) + 1]);
+      const float2 o = make_float2(ko[2 * (i % EB)], ko[2 * (i % EB) + 1]);
       const float2 d = csub(psi1, cmul(p, o));
       const float2 uo = cscale(cmulc(p, d), inv_pm);
       const size_t oi = obase + y * orow + xl;
@@ -404,10 +441,14 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   }
 #undef EPIE_LD_O
 #undef EPIE_ST_O
-#ifdef EPIE_PHASE_CLOCKS
+  // every thread's tensor-memory reads are done before warp 0 frees it
+  tc_fence_before();
   __syncthreads();
   EPIE_PHASE(13);
-#endif
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tm_base, C::TM_COLS);
+  }
 }
 
 template <int N, int CL, int NT, typename IT>
@@ -426,6 +467,16 @@ cudaError_t launch_fused_t(const GroupArgs &a, cudaStream_t st) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
+    // A TMEM allocation blocks until columns are free, and CTAs of a cluster
+    // wait for each other, so every CTA that can be resident on an SM must
+    // find its columns at once: at most 512 in total.  Any step kernel is
+    // held to 2 resident CTAs of <= 256 columns, or 1 of <= 512 (the tcgen05
+    // GEMM's shared memory keeps it off SMs that hold a step kernel).
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (occ < 1 || occ * C::TM_COLS > 512 || (occ > 1 && C::TM_COLS > 256))
+      return cudaErrorInvalidConfiguration;
     configured[dev] = true;
   }
   if (a.n_members <= 0) return cudaSuccess;
