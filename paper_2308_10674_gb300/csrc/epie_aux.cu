@@ -61,7 +61,8 @@ __global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restr
 // new probe (FP32 comparison picks the element).  A block of 32 x 8 threads
 // covers 64 complex elements (two per thread, 16-byte loads); thread row r
 // sums members r, r+8, ... in order and the 8 row sums are added in row
-// order, so the result does not depend on scheduling.
+// order, so the result does not depend on scheduling.  The partials are read
+// once, with the streaming hint, so their lines leave L2 before the object's.
 __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ P,
                                                           const float2 *__restrict__ part,
                                                           int n_members, int K, float scale,
@@ -84,17 +85,17 @@ __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ 
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     int m = ty;
     for (; m + 24 < n_members; m += 32) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i);
-      const float4 a1 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 8) * K + i);
-      const float4 a2 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 16) * K + i);
-      const float4 a3 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 24) * K + i);
+      const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i));
+      const float4 a1 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 8) * K + i));
+      const float4 a2 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 16) * K + i));
+      const float4 a3 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 24) * K + i));
       acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
       acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
       acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
       acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
     }
     for (; m < n_members; m += 8) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i);
+      const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i));
       acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
     }
     acc_sh[ty][tx] = acc;
