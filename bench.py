@@ -533,6 +533,20 @@ def run_multiscan(args):
     return 0
 
 
+def adjoint_roofline(n, ms, N=128):
+    """The gradient evaluation runs four 2-D transforms per position (the
+    probe's Fourier shift, the far field, the far field's adjoint and the
+    shift's adjoint) on the FP32 pipes: 4 x 5 K log2 K FLOP, against the FP32
+    FMA peak."""
+    pk, _ = peaks()
+    flops = 4 * 5 * N * N * math.log2(N * N)
+    achieved = n * flops / (ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "flops_per_position": flops,
+            "note": "whole gradient call (all its kernels) per position"}
+
+
 def run_adjoint(args):
     """Amplitude-loss gradients (object, probe, sub-pixel positions) at 128^2:
     4,096 jittered-raster positions, object 642 x 642; gradient evaluations
@@ -573,6 +587,7 @@ def run_adjoint(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{n} jittered-raster positions, 128^2 uint16, object "
                                    f"{d['H']}x{d['W']}, gradients for object, probe, shifts"},
+            "roofline": adjoint_roofline(n, ms),
             "adam_200": {"loss_first": losses[0], "loss_last": losses[-1],
                          "finite": bool(np.all(np.isfinite(losses)))}}
     print(json.dumps(line), flush=True)
