@@ -330,11 +330,17 @@ def run_ours(args):
     with Clocks(device) as clk:
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one event at every step boundary too (each step ends with a host read
+        # of its sweep error, so they add no wait between launches)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for k in range(args.steps):
             errs.append(float(step_device()[0]))
+            evs[k + 1].record(stream)
         ev1.record(stream)
         barrier()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     dev_str = f"cuda:{device}"
     value, elapsed_s = replica_rate(n * args.steps, ev0.elapsed_time(ev1) / 1e3, dev_str)
     elapsed_ms = elapsed_s * 1e3
@@ -406,6 +412,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(args, d), "frames": n, "N": N,
