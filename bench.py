@@ -386,7 +386,7 @@ def run_ours(args):
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     tr = measured_traffic()
     traffic = None if tr is None else tr["dram_bytes_per_frame"] * frames_per_launch
-    hbm_bytes_per_frame = N * N * 2  # the uint16 intensity frame
+    hbm_bytes_per_frame = N * N * 4  # the frame's fp32 measured-amplitude tile
     hbm_achieved = hbm_bytes_per_frame * frames_per_launch / (kernel_avg_ms / 1e3) / 1e9
     # measured FP32 FMA-chain rate, after the timed regions (its clock beside it)
     try:

@@ -91,6 +91,11 @@ struct epie_ctx {
   int32_t *pos_d = nullptr, *order_d = nullptr;
   float *dark_d = nullptr;
   bool has_dark = false;
+  // fused path: measured amplitudes sqrt(max(I - dark, 0)) of every frame in
+  // FFT order (fp32) and their intensity sums (FP64), derived at append and
+  // re-derived when the dark field changes
+  float *amp = nullptr;
+  double *amp_isum = nullptr;
   float2 *probe_part = nullptr;
   int part_cap = 0;             // members the probe_part buffer holds
   double *err_part = nullptr, *isum_part = nullptr;
@@ -294,6 +299,8 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, bool o_early
   a.accO = mb ? h->accO : nullptr;
   a.cnt = mb ? h->cnt : nullptr;
   a.o_early = o_early && !h->ktime;  // timing events sit between the launches
+  a.amp = h->amp;
+  a.amp_isum = h->amp_isum;
   if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
     CK(epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st));
     a.omax2_global = h->omax_glob;
@@ -428,6 +435,8 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
       a.accO = mb ? h->accO : nullptr;
       a.cnt = mb ? h->cnt : nullptr;
       a.o_early = g > 0;
+      a.amp = h->amp;
+      a.amp_isum = h->amp_isum;
       if (h->cfg.omax_mode == EPIE_OMAX_GLOBAL) {
         ce = epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st);
         a.omax2_global = h->omax_glob;
@@ -553,7 +562,7 @@ int epie_destroy(epie_t h) {
     void *dev[] = {h->gstart_d, h->err_sweep, h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
                    h->probe_part, h->err_part, h->isum_part, h->pmax2, h->omax_glob,
                    h->omax_tmp, h->err_out, h->flag_d, h->O_keep, h->P_keep, h->psi,
-                   h->omax_m, h->accO, h->cnt, h->stage_d};
+                   h->omax_m, h->accO, h->cnt, h->stage_d, h->amp, h->amp_isum};
     for (void *p : dev)
       if (p) cudaFree(p);
     for (void *p : h->stage_h)
@@ -658,6 +667,10 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   IK(cudaMalloc(&h->pos_d, sizeof(int32_t) * 2 * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->order_d, sizeof(int32_t) * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->dark_d, sizeof(float) * h->K));
+  if (c.path == EPIE_PATH_FUSED) {
+    IK(cudaMalloc(&h->amp, sizeof(float) * h->K * static_cast<size_t>(cap)));
+    IK(cudaMalloc(&h->amp_isum, sizeof(double) * static_cast<size_t>(cap)));
+  }
   IK(cudaMalloc(&h->err_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->isum_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->pmax2, sizeof(unsigned long long) * 2));
@@ -736,21 +749,24 @@ int epie_set_dark(epie_t h, const float *dark) {
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(h->mu);
   CK(cudaSetDevice(h->cfg.device));
-  if (!dark) {
-    h->has_dark = false;
-    return EPIE_OK;
-  }
-  float *tmp = reinterpret_cast<float *>(h->stage_d);
   CK(cudaStreamWaitEvent(h->st, h->ev_up, 0));
-  if (h->cfg.flags & EPIE_FRAMES_FFT_ORDER) {
-    CK(cudaMemcpyAsync(h->dark_d, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
-  } else {
-    CK(cudaMemcpyAsync(tmp, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
-    CK(epie::launch_dark_ingest(tmp, h->dark_d, h->cfg.N, h->st));
+  if (dark) {
+    float *tmp = reinterpret_cast<float *>(h->stage_d);
+    if (h->cfg.flags & EPIE_FRAMES_FFT_ORDER) {
+      CK(cudaMemcpyAsync(h->dark_d, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
+    } else {
+      CK(cudaMemcpyAsync(tmp, dark, sizeof(float) * h->K, cudaMemcpyHostToDevice, h->st));
+      CK(epie::launch_dark_ingest(tmp, h->dark_d, h->cfg.N, h->st));
+      h->launches_total += 1;
+    }
+  }
+  h->has_dark = dark != nullptr;
+  if (h->amp && h->n_frames > 0) {  // the frames' amplitudes follow the dark field
+    CK(epie::launch_amp_ingest(h->frames, h->cfg.intensity_dtype, h->has_dark ? h->dark_d : nullptr,
+                               h->amp, h->amp_isum, 0, h->n_frames, h->cfg.N, h->st));
     h->launches_total += 1;
   }
   CK(cudaStreamSynchronize(h->st));
-  h->has_dark = true;
   return EPIE_OK;
 }
 
@@ -807,6 +823,12 @@ static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t
       CK(epie::launch_ingest(h->stage_d, dst, m, N, static_cast<int>(es), h->up));
       h->launches_total += 1;
     }
+  }
+  if (h->amp) {
+    CK(epie::launch_amp_ingest(h->frames, h->cfg.intensity_dtype,
+                               h->has_dark ? h->dark_d : nullptr, h->amp, h->amp_isum,
+                               h->n_frames, n, N, h->up));
+    h->launches_total += 1;
   }
   CK(cudaMemcpyAsync(h->pos_d + 2 * static_cast<size_t>(h->n_frames), pos,
                      sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, h->up));

@@ -4,6 +4,7 @@
 // (gather / modulus / update) that runs the same step with cuFFT in between.
 #include <cuda_fp16.h>
 
+#include "../../include/epie.h"
 #include "epie_fft.cuh"
 #include "epie_internal.h"
 
@@ -362,6 +363,52 @@ cudaError_t launch_average(const float2 *const *src, int k, float2 *out, long lo
 
 cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st) {
   fill_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+namespace {
+// Measured amplitude of frames [f0, f0 + n) in FFT order: amp = sqrt(max(I -
+// dark, 0)), and the frame's sum of max(I - dark, 0) in FP64.  One block per
+// frame; each thread sums a fixed set of elements and the block adds the
+// thread sums in a fixed order, so the sums do not depend on scheduling.
+template <typename IT>
+__global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__ frames,
+                                                         const float *__restrict__ dark,
+                                                         float *__restrict__ amp,
+                                                         double *__restrict__ isum, int f0, int K) {
+  __shared__ double sh[1024];
+  const size_t base = static_cast<size_t>(f0 + blockIdx.x) * K;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < K; i += 1024) {
+    float v = ival(frames[base + i]);
+    if (dark) v -= dark[i];
+    v = fmaxf(v, 0.f);
+    s += static_cast<double>(v);
+    amp[base + i] = sqrtf(v);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) isum[f0 + blockIdx.x] = sh[0];
+}
+}  // namespace
+
+cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
+                              double *isum, int f0, int n, int N, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int K = N * N;
+  if (itype == EPIE_U16)
+    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp, isum,
+                                          f0, K);
+  else if (itype == EPIE_F16)
+    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const __half *>(frames), dark, amp, isum,
+                                          f0, K);
+  else
+    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const float *>(frames), dark, amp, isum, f0,
+                                          K);
   return cudaGetLastError();
 }
 

@@ -73,6 +73,7 @@ struct FusedCfg {
   static_assert(E * NT == N * WC, "tile must split evenly over threads");
   static_assert(I_BYTES % 16 == 0, "bulk copy size");
   static_assert(OFF_IRAW % 16 == 0, "bulk copy destination alignment");
+  static_assert(OFF_I % 16 == 0 && IF_BYTES % 16 == 0, "amplitude tile bulk copy");
 };
 
 template <int N>
@@ -161,10 +162,17 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   const uint32_t tm = tm_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
                       static_cast<uint32_t>((warp >> 2) * 64);
   if (tid == 0) {
-    // the frame is read once per sweep: keep it from evicting the object
-    mbar_arrive_expect_tx(bar, C::I_BYTES);
-    bulk_g2s_hint(iraw, frame + static_cast<size_t>(crank) * HR * N, C::I_BYTES, bar,
-                  l2_evict_first_policy());
+    // the frame is read once per sweep: keep it from evicting the object.
+    // With derived amplitudes the tile arrives ready for the modulus.
+    if (a.amp) {
+      mbar_arrive_expect_tx(bar, C::IF_BYTES);
+      bulk_g2s_hint(itile, a.amp + static_cast<size_t>(f) * N * N + static_cast<size_t>(crank) * HR * N,
+                    C::IF_BYTES, bar, l2_evict_first_policy());
+    } else {
+      mbar_arrive_expect_tx(bar, C::I_BYTES);
+      bulk_g2s_hint(iraw, frame + static_cast<size_t>(crank) * HR * N, C::I_BYTES, bar,
+                    l2_evict_first_policy());
+    }
   }
   for (int m = tid; m < N; m += NT) tw[m] = a.twiddle[m];
 
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
   ok = __all_sync(0xffffffffu, ok);  // warp-uniform: phase 3 reads TMEM warp-collectively
   float isum_t = 0.f;  // sum I of this thread's tile elements
-  {
+  if (!a.amp) {
     // intensity tile -> float max(I - dark, 0), in place: the raw tile sits
     // at the top of the float tile, so every raw value is read (and the dark
     // field fetched with one latency) before any float is written
@@ -347,7 +355,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       ss = warp_sum_f(ss);
       if (lane == 0) {
         a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(es);
-        a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(ss);
+        a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] =
+            a.amp ? (crank == 0 ? a.amp_isum[f] : 0.0) : static_cast<double>(ss);
       }
     }
   }

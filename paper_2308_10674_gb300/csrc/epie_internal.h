@@ -56,6 +56,11 @@ struct GroupArgs {
   // the same sweep: that reduction waited for the previous step kernel, so
   // the object is final and may be read before this kernel's dependency wait
   int o_early;
+  // the frames' measured amplitudes sqrt(max(I - dark, 0)) in FFT order and
+  // their per-frame intensity sums, derived at append; when set, the step
+  // kernel copies its amplitude tile instead of converting raw intensities
+  const float *amp;
+  const double *amp_isum;
 };
 
 // error-flag bits written by kernels
@@ -98,6 +103,10 @@ cudaError_t launch_average(const float2 *const *src, int k, float2 *out, long lo
 cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st);
 // dark field: DC-centred float -> FFT order
 cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t st);
+// amp[f] = sqrt(max(I_f - dark, 0)) (FFT order, fp32) and isum[f] = sum of
+// max(I_f - dark, 0) (FP64) for frames [f0, f0 + n) of the frame set
+cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
+                              double *isum, int f0, int n, int N, cudaStream_t st);
 
 // plain unfused path pieces
 cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,
