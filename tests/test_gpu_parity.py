@@ -419,3 +419,29 @@ def test_frames_in_fft_order_flag():
             outs.append((eng.object(), eng.probe(), e))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_dark_field_set_after_append_rederives_amplitudes():
+    """The measured amplitudes are derived at append and re-derived when the
+    dark field changes: setting (or clearing) the dark field after the frames
+    gives the same bits as setting it (or never setting it) before."""
+    d = synth.small_scan(256, 3, 3, 120, seed=23)
+    rng = np.random.default_rng(8)
+    dark = (30.0 * rng.random((256, 256))).astype(np.float32)
+
+    def run(order):
+        with engine(d, B.EPIE_COLOURED, flat_start(d)) as eng:
+            for op in order:
+                if op == "dark":
+                    eng.set_dark(dark)
+                elif op == "clear":
+                    eng.set_dark(None)
+                else:
+                    eng.append(d["frames"], d["pos"])
+            e = eng.iterate(2)
+            return eng.object(), eng.probe(), e
+
+    for a, b in [(("dark", "frames"), ("frames", "dark")),
+                 (("frames",), ("dark", "frames", "clear"))]:
+        ra, rb = run(a), run(b)
+        assert all(np.array_equal(x, y) for x, y in zip(ra, rb)), (a, b)
