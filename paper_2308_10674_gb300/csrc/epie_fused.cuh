@@ -8,18 +8,23 @@
 //            [c N/CL, (c+1) N/CL) and transforms every column (FFT along y);
 //   swap     all-to-all transpose through distributed shared memory: CTA c
 //            now holds the row block [c N/CL, (c+1) N/CL) of the spectrum;
-//   phase 2  FFT along x, modulus replacement with sqrt(I) (intensity tile
-//            staged by a bulk TMA copy issued at kernel start, dark field
-//            subtracted, error terms summed), inverse FFT along x;
+//   phase 2  FFT along x, modulus replacement with sqrt(I) (the frame's
+//            measured-amplitude tile, derived at append, arrives by a bulk
+//            TMA copy issued at kernel start; without derived amplitudes the
+//            raw intensity tile is copied and converted here, dark field
+//            subtracted), error terms summed, inverse FFT along x;
 //   swap     transpose back to column blocks;
 //   phase 3  inverse FFT along y -> psi', Delta = psi' - psi, object patch
 //            update with conj(P)/max|P|^2 (patches of a group are disjoint, so
 //            the writes never race) and the probe-update partial
-//            beta conj(O_old)/max|O_old|^2 Delta for the group reduction.
+//            beta conj(O_old)/max|O_old|^2 Delta for the group reduction;
+//            the object patch and probe values of phase 1 come back from
+//            tensor memory, where each thread parked them.
 //
-// For N <= 128 one CTA holds the whole frame (CL = 1) and the swaps are
-// plain shared-memory re-indexing.  Shared memory holds one tile per CTA,
-// the twiddle table, the intensity tile and a few reduction slots.
+// At N = 64 one CTA holds the whole frame (CL = 1) and the swaps are plain
+// shared-memory re-indexing.  Shared memory holds one tile per CTA, the
+// twiddle table, the amplitude (or intensity) tile and a few reduction
+// slots.
 #pragma once
 
 #include <cooperative_groups.h>
