@@ -158,7 +158,9 @@ typedef struct {
  * seed 0, device 0, own stream, no flags, no class cap, EPIE_GEMM_BF16X3. */
 EPIE_API void epie_config_default(epie_config *cfg);
 
-/* Creates a handle and allocates every device buffer the configuration needs.
+/* Creates a handle and allocates every device buffer the configuration needs:
+ * on the fused path that includes capacity*N*N fp32 measured amplitudes
+ * beside the capacity*N*N frames of intensity_dtype.
  * probe0: N*N complex (required).  object0: obj_h*obj_w complex, or NULL for
  * an object of ones (the paper's "identity" start, Sec. "Results").
  * Returns EPIE_EINVAL for a bad configuration, EPIE_ECUDA when the device
@@ -167,7 +169,11 @@ EPIE_API int epie_init(epie_t *out, const epie_config *cfg, const float *probe0,
 
 /* Dark-offset field subtracted from every frame (clamped at 0) before the
  * modulus replacement.  dark: N*N float32 in the detector (DC-centred) layout
- * of the frames, or NULL to remove it.  Takes effect at the next sweep. */
+ * of the frames (FFT order with EPIE_FRAMES_FFT_ORDER), or NULL to remove it.
+ * Takes effect at the next sweep.  On the fused path the frames' measured
+ * amplitudes sqrt(max(I - dark, 0)) are derived at append and re-derived here
+ * for every frame already appended (one pass over the frame set); the call
+ * returns when that is done. */
 EPIE_API int epie_set_dark(epie_t h, const float *dark);
 
 /* Live ingest (paper, Sec. "Extensions of the ePIE implementation"): appends
