@@ -58,11 +58,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--workload", default="live",
-                    choices=["live", "multiscan", "adjoint", "live-schedule", "tc-gemm"],
+                    choices=["live", "multiscan", "adjoint", "live-schedule", "tc-gemm",
+                             "oracle-cores"],
                     help="live: the headline 256^2 live scan; multiscan: eight uneven scans "
                          "sweeping concurrently; adjoint: amplitude-loss gradients at 128^2; "
                          "live-schedule: the whole live run, chunk by chunk; tc-gemm: the "
-                         "tcgen05 GEMM of the DFT-as-GEMM path on its shapes")
+                         "tcgen05 GEMM of the DFT-as-GEMM path on its shapes; oracle-cores: "
+                         "the FP64 oracle on one host core and on all of them (no GPU)")
     ap.add_argument("--sweeps-per-chunk", type=int, default=50,
                     help="live-schedule: sweeps after each chunk (and at the end)")
     return ap.parse_args()
@@ -764,6 +766,53 @@ def run_tc_gemm(args):
     return 0
 
 
+def _oracle_window(job):
+    """One coloured FP64 oracle sweep over a window of the workload's frames
+    from the paper's flat start; returns its compute seconds."""
+    frames, pos, dark, P0, H, W, N = job
+    from oracle import oracle as orc
+    I_all = orc.prepare_intensity(frames, dark)
+    O = np.ones((H, W), np.complex128)
+    P = P0.astype(np.complex64).astype(np.complex128)
+    t = time.perf_counter()
+    col, ncls = orc.colour_greedy(pos, N)
+    order, gs = orc.order_coloured(5, 0, col, ncls)
+    orc.sweep_groups(O, P, I_all, pos, order, gs)
+    return time.perf_counter() - t
+
+
+def run_oracle_cores(args):
+    """The FP64 oracle as it stands on the host: one coloured sweep over a
+    500-frame window of the live workload on one core, then one window per
+    core on all cores at once (disjoint windows, one process each).  No GPU."""
+    import multiprocessing as mp
+    d = workload(args)
+    n_w, cores = 500, os.cpu_count() or 1
+    n = len(d["pos"])
+    jobs = []
+    for k in range(cores):
+        a = (k * n_w) % (n - n_w)
+        jobs.append((d["frames"][a:a + n_w], d["pos"][a:a + n_w], d["dark"], d["P0"], d["H"],
+                     d["W"], d["N"]))
+    t1 = _oracle_window(jobs[0])
+    with mp.get_context("spawn").Pool(cores) as pool:
+        times = pool.map(_oracle_window, jobs)
+    one = n_w / t1
+    all_cores = sum(n_w / t for t in times)
+    line = {"metric": "FP64 oracle frame-updates/s on the host, one core and all cores",
+            "value": all_cores, "unit": UNIT, "n_gpus": 0, "steps": 1, "warmup": 0,
+            "ms_per_step": max(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args, d), "window_frames": n_w},
+            "cpu_baseline": {"value": all_cores, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} disjoint {n_w}-frame windows, one coloured "
+                                       f"sweep each, one process per core, concurrently"},
+            "one_core": {"value": one, "seconds": t1},
+            "per_core_seconds": times}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -776,6 +825,8 @@ def main():
         return run_live_schedule(args)
     if args.workload == "tc-gemm":
         return run_tc_gemm(args)
+    if args.workload == "oracle-cores":
+        return run_oracle_cores(args)
     return run_ours(args)
 
 
