@@ -228,8 +228,7 @@ __global__ void __launch_bounds__(AdjCfg<N, CL>::NT, 1) amp_grad_kernel(AdjArgs 
     const float2 p = ps[yl * N + x];
     const float2 go = cmulc(p, gpsi);
     float2 *dst = gOrow + static_cast<size_t>(yl) * a.W + x;
-    atomicAdd(&dst->x, go.x);
-    atomicAdd(&dst->y, go.y);
+    atomicAdd(dst, go);  // one 8-byte vector reduction
     slab[RowB<N, CL>::at(yl, x)] = cmulc(Orow[static_cast<size_t>(yl) * a.W + x], gpsi);
   }
   __syncthreads();
@@ -251,8 +250,7 @@ __global__ void __launch_bounds__(AdjCfg<N, CL>::NT, 1) amp_grad_kernel(AdjArgs 
     gdy = fmaf(w * freq<N>(y), im, gdy);
     gdx = fmaf(w * freq<N>(x), im, gdx);
     const float2 acc = cmul(gz, make_float2(ph.x, -ph.y));
-    atomicAdd(&a.gFP[y * N + x].x, acc.x);
-    atomicAdd(&a.gFP[y * N + x].y, acc.y);
+    atomicAdd(&a.gFP[y * N + x], acc);
   }
   const float s0 = warp_sum_f(loss), s1 = warp_sum_f(gdy), s2 = warp_sum_f(gdx);
   if (lane == 0) {
