@@ -59,19 +59,21 @@ __global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restr
 // ---------------------------------------------------------------- probe
 
 // P += scale * sum_{m < n_members} part[m], then the FP64 max|P|^2 of the
-// new probe (FP32 comparison picks the element).  A block of 32 x 8 threads
-// covers 64 complex elements (two per thread, 16-byte loads); thread row r
-// sums members r, r+8, ... in order and the 8 row sums are added in row
-// order, so the result does not depend on scheduling.  The partials are read
-// once, with the streaming hint, so their lines leave L2 before the object's.
-__global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ P,
-                                                          const float2 *__restrict__ part,
-                                                          int n_members, int K, float scale,
-                                                          unsigned long long *pmax2_next,
-                                                          const int32_t *gstart, int group,
-                                                          int mean) {
-  __shared__ float4 acc_sh[8][32];
-  __shared__ double sh[8];
+// new probe (FP32 comparison picks the element).  A block of 32 x PR_ROWS
+// threads covers 64 complex elements (two per thread, 16-byte loads); thread
+// row r sums members r, r + PR_ROWS, ... in order and the row sums are added
+// in row order, so the result does not depend on scheduling.  The partials
+// are read once, with the streaming hint, so their lines leave L2 before the
+// object's.
+#ifndef EPIE_PROBE_ROWS
+#define EPIE_PROBE_ROWS 8
+#endif
+constexpr int PR_ROWS = EPIE_PROBE_ROWS, PR_THREADS = 32 * PR_ROWS;
+__global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
+    float2 *__restrict__ P, const float2 *__restrict__ part, int n_members, int K, float scale,
+    unsigned long long *pmax2_next, const int32_t *gstart, int group, int mean) {
+  __shared__ float4 acc_sh[PR_ROWS][32];
+  __shared__ double sh[PR_THREADS / 32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (gstart) {  // group size from the device table
     n_members = gstart[group + 1] - gstart[group];
@@ -81,22 +83,23 @@ __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ 
   grid_dependents_launch();
   float best = -1.f;
   float2 bv = make_float2(0.f, 0.f);
+  auto ld = [&](int m, int i) {
+    return __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i));
+  };
   for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
     const int i = base + 2 * tx;  // K is a multiple of 64
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     int m = ty;
-    for (; m + 24 < n_members; m += 32) {
-      const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i));
-      const float4 a1 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 8) * K + i));
-      const float4 a2 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 16) * K + i));
-      const float4 a3 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m + 24) * K + i));
+    for (; m + 3 * PR_ROWS < n_members; m += 4 * PR_ROWS) {
+      const float4 a0 = ld(m, i), a1 = ld(m + PR_ROWS, i), a2 = ld(m + 2 * PR_ROWS, i),
+                   a3 = ld(m + 3 * PR_ROWS, i);
       acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
       acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
       acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
       acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
     }
-    for (; m < n_members; m += 8) {
-      const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(part + static_cast<size_t>(m) * K + i));
+    for (; m < n_members; m += PR_ROWS) {
+      const float4 a0 = ld(m, i);
       acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
     }
     acc_sh[ty][tx] = acc;
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ 
     if (ty == 0) {
       float4 t = acc_sh[0][tx];
 #pragma unroll
-      for (int r = 1; r < 8; ++r) {
+      for (int r = 1; r < PR_ROWS; ++r) {
         const float4 u = acc_sh[r][tx];
         t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
       }
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256) probe_reduce_kernel(float2 *__restrict__ 
     __syncthreads();
   }
   double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
-  d = block_max<256>(d, sh);
+  d = block_max<PR_THREADS>(d, sh);
   if (threadIdx.x == 0) atomic_max_pos_double(pmax2_next, d);
 }
 
@@ -422,7 +425,7 @@ cudaError_t launch_probe_reduce(float2 *P, const float2 *part, int n_members, in
   const int K = N * N;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid_for(K, 64, 152 * 8), 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(PR_THREADS, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -439,7 +442,7 @@ cudaError_t launch_probe_reduce_table(float2 *P, const float2 *part, const int32
   const int K = N * N;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid_for(K, 64, 152 * 8), 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(PR_THREADS, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
