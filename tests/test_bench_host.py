@@ -1,0 +1,42 @@
+"""Host-side pieces of bench.py (no GPU): the traffic record's key ignores
+comment edits but not code edits, the committed record parses, and the
+replica rate of a single process is units over seconds."""
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2308_10674_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("epie_fft.cuh", "epie_fused.cuh", "epie_fused_256.cu"):
+        shutil.copy(os.path.join(ROOT, "paper_2308_10674_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.source_hash()
+    p = csrc / "epie_fused.cuh"
+    p.write_text(p.read_text() + "\n// a new comment line\n\n")
+    assert bench.source_hash() == h0
+    p.write_text(p.read_text().replace("constexpr int EB", "constexpr  int EB", 1))
+    assert bench.source_hash() != h0
+
+
+def test_committed_traffic_record_parses():
+    rec = {}
+    with open(os.path.join(ROOT, "profiles", "fused_256_traffic.txt")) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    assert len(rec["source_hash"]) == 16
+    assert float(rec["dram_bytes_per_frame"]) > 256 * 256 * 2
+
+
+def test_replica_rate_single_process():
+    value, secs = bench.replica_rate(1000, 2.0)
+    assert value == pytest.approx(500.0) and secs == pytest.approx(2.0)
