@@ -59,13 +59,14 @@ def parse():
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--workload", default="live",
                     choices=["live", "multiscan", "adjoint", "live-schedule", "tc-gemm",
-                             "oracle-cores", "parallel"],
+                             "oracle-cores", "parallel", "gemm-path"],
                     help="live: the headline 256^2 live scan; multiscan: eight uneven scans "
                          "sweeping concurrently; adjoint: amplitude-loss gradients at 128^2; "
                          "live-schedule: the whole live run, chunk by chunk; tc-gemm: the "
                          "tcgen05 GEMM of the DFT-as-GEMM path on its shapes; oracle-cores: "
                          "the FP64 oracle on one host core and on all of them (no GPU); "
-                         "parallel: the paper's disjoint-subset averaging scheme")
+                         "parallel: the paper's disjoint-subset averaging scheme; gemm-path: "
+                         "the DFT-as-GEMM path at every operand precision against the FFT path")
     ap.add_argument("--sweeps-per-chunk", type=int, default=50,
                     help="live-schedule: sweeps after each chunk (and at the end)")
     return ap.parse_args()
@@ -810,6 +811,54 @@ def run_parallel(args):
     return 0
 
 
+def run_gemm_path(args):
+    """The step with its 2-D DFT done as dense GEMMs, at every operand
+    precision (cuBLAS and the engine's own tcgen05 kernel), against the fused
+    FFT path: mini-batch sweeps (B = 1024) over 16,384 Fermat-spiral positions
+    of the live model (geometry B) at 128^2 and 256^2."""
+    import torch
+    from paper_2308_10674_gb300 import _binding as B, synth
+    torch.cuda.set_device(0)
+    V = [("fused FFT", B.EPIE_PATH_FUSED, 0), ("bf16", B.EPIE_PATH_GEMM, B.EPIE_GEMM_BF16),
+         ("tf32", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TF32),
+         ("bf16x3", B.EPIE_PATH_GEMM, B.EPIE_GEMM_BF16X3),
+         ("fp32 emulation", B.EPIE_PATH_GEMM, B.EPIE_GEMM_FP32EMU),
+         ("tc bf16", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_BF16),
+         ("tc bf16x3", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_BF16X3),
+         ("tc tf32", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_TF32),
+         ("tc tf32x3", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_TF32X3)]
+    rows = []
+    with Clocks(0) as clk:
+        for N in (128, 256):
+            n = 16384
+            d = synth.live_scan(N=N, n=n, geometry="B", seed=0, workers=args.workers,
+                                fwhm=60.0 * N / 256)
+            for name, path, prec in V:
+                eng = B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=n,
+                               mode=B.EPIE_MINIBATCH, batch=1024, seed=5, path=path,
+                               gemm_precision=prec)
+                eng.set_dark(d["dark"])
+                eng.append(d["frames"], d["pos"])
+                eng.iterate(max(1, args.warmup))
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                errs = eng.iterate(args.steps)
+                dt = (time.perf_counter() - t) / args.steps
+                eng.close()
+                rows.append({"N": N, "path": name, "frame_updates_per_s": n / dt,
+                             "ms_per_sweep": dt * 1e3, "sweep_error": float(errs[-1])})
+    ref = [r for r in rows if r["N"] == 256 and r["path"] == "tc bf16x3"][0]
+    line = {"metric": "DFT-as-GEMM ePIE frame-updates/s at 256^2 (tcgen05 split bf16), "
+                      "mini-batch B = 1024",
+            "value": ref["frame_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ref["ms_per_sweep"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": "16,384 Fermat-spiral positions, geometry B, mini-batch 1024"},
+            "clocks": clk.summary(), "paths": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _oracle_window(job):
     """One coloured FP64 oracle sweep over a window of the workload's frames
     from the paper's flat start; returns its compute seconds."""
@@ -873,6 +922,8 @@ def main():
         return run_oracle_cores(args)
     if args.workload == "parallel":
         return run_parallel(args)
+    if args.workload == "gemm-path":
+        return run_gemm_path(args)
     return run_ours(args)
 
 
