@@ -114,7 +114,7 @@ typedef struct epie_ctx *epie_t;
 #define EPIE_GEMM_TC_BF16 4  /* bf16 operands, this library's tcgen05 kernel     */
 #define EPIE_GEMM_TC_BF16X3 5 /* split bf16, this library's tcgen05 kernel: the
                                 three products share one TMEM accumulator       */
-#define EPIE_GEMM_TC_TF32 6  /* fp32 operands read as tf32, own tcgen05 kernel  */
+#define EPIE_GEMM_TC_TF32 6  /* operands rounded to nearest tf32, own tcgen05 kernel */
 #define EPIE_GEMM_TC_TF32X3 7 /* split tf32 (x = hi + lo, hi = x with its low 13
                                 mantissa bits cleared): hi*hi + hi*lo + lo*hi in
                                 one TMEM accumulator, own tcgen05 kernel        */

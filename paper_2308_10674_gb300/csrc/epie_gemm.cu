@@ -21,7 +21,8 @@
 //     on this engine's own tcgen05 kernel (epie_tc_gemm.cu), the three
 //     split products accumulated in one tensor-memory accumulator
 //   EPIE_GEMM_TC_TF32, EPIE_GEMM_TC_TF32X3: the same kernel on fp32 operands
-//     read as tf32 (kind::tf32); the split form takes hi = x with its low 13
+//     read as tf32 (kind::tf32); the plain form rounds its operands to the
+//     nearest tf32 first, the split form takes hi = x with its low 13
 //     mantissa bits cleared and lo = x - hi, both tf32-exact
 // Twiddles are evaluated in double precision on the host (exact k j mod N).
 #include <cublas_v2.h>
@@ -143,6 +144,17 @@ __global__ void split_tf32_kernel(const float *__restrict__ x, float *__restrict
   }
 }
 
+// x rounded to the nearest tf32 value (ties to even; finite inputs)
+__global__ void round_tf32_kernel(const float *__restrict__ x, float *__restrict__ r,
+                                  long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    uint32_t u = __float_as_uint(x[i]);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    r[i] = __uint_as_float(u & 0xFFFFE000u);
+  }
+}
+
 int grid_for(long long n, int nt, int cap) {
   long long g = (n + nt - 1) / nt;
   if (g > cap) g = cap;
@@ -162,6 +174,16 @@ bool split_precision(int p) {
   return p == EPIE_GEMM_BF16 || p == EPIE_GEMM_BF16X3 || tc_bf16_precision(p);
 }
 bool x3_precision(int p) { return p == EPIE_GEMM_BF16X3 || p == EPIE_GEMM_TC_BF16X3; }
+
+// nearest tf32 value (ties to even) of a finite fp32 value
+float tf32_round(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  u &= 0xFFFFE000u;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
 
 float tf32_hi(float v) {
   uint32_t u;
@@ -184,9 +206,18 @@ int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool i
   // of frames, so the rows past the group (N = 64, odd group) exist and
   // their results are never read
   const long long mrows = (rows + 127) / 128 * 128;
-  if (g->precision == EPIE_GEMM_TC_TF32)
-    return tc_gemm_tf32(srcf, nullptr, inverse ? g->Ti : g->Tf, nullptr, dstf, mrows, n2, n2, n2,
-                        1, err_flag, st, err);
+  if (g->precision == EPIE_GEMM_TC_TF32) {
+    // operands rounded to nearest tf32 (the tensor cores would truncate)
+    round_tf32_kernel<<<grid_for(rows * n2, 256, 152 * 16), 256, 0, st>>>(srcf, g->F_hi,
+                                                                           rows * n2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return EPIE_ECUDA;
+    }
+    return tc_gemm_tf32(g->F_hi, nullptr, inverse ? g->Ti : g->Tf, nullptr, dstf, mrows, n2, n2,
+                        n2, 1, err_flag, st, err);
+  }
   if (g->precision == EPIE_GEMM_TC_TF32X3) {
     split_tf32_kernel<<<grid_for(rows * n2, 256, 152 * 16), 256, 0, st>>>(srcf, g->F_hi, g->F_lo,
                                                                            rows * n2);
@@ -317,6 +348,17 @@ GemmPath *gemm_path_create(int N, int precision, cudaStream_t st, std::string *e
          split(g->Tf, g->Tft_hi, g->Tft_lo, static_cast<long long>(Tf.size()), st) == cudaSuccess &&
          split(g->Ti, g->Tit_hi, g->Tit_lo, static_cast<long long>(Ti.size()), st) == cudaSuccess &&
          cudaStreamSynchronize(st) == cudaSuccess;
+    if (ok && precision == EPIE_GEMM_TC_TF32) {
+      // the tensor cores keep the top 10 mantissa bits of an fp32 operand; give
+      // them the twiddles already rounded to nearest tf32
+      std::vector<float> fr(Tft.size()), ir(Tit.size());
+      for (size_t i = 0; i < Tft.size(); ++i) {
+        fr[i] = tf32_round(Tft[i]);
+        ir[i] = tf32_round(Tit[i]);
+      }
+      ok = cudaMemcpy(g->Tf, fr.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(g->Ti, ir.data(), tb, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (ok && precision == EPIE_GEMM_TC_TF32X3) {
       std::vector<float> fh(Tft.size()), fl(Tft.size()), ih(Tit.size()), il(Tit.size());
       for (size_t i = 0; i < Tft.size(); ++i) {
@@ -362,9 +404,10 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
     if (ok && x3_precision(g->precision))
       ok = cudaMalloc(&g->D_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
   }
+  if (ok && tc_tf32_precision(g->precision))
+    ok = cudaMalloc(&g->F_hi, sizeof(float) * 2 * K * cap) == cudaSuccess;
   if (ok && g->precision == EPIE_GEMM_TC_TF32X3)
-    ok = cudaMalloc(&g->F_hi, sizeof(float) * 2 * K * cap) == cudaSuccess &&
-         cudaMalloc(&g->F_lo, sizeof(float) * 2 * K * cap) == cudaSuccess;
+    ok = cudaMalloc(&g->F_lo, sizeof(float) * 2 * K * cap) == cudaSuccess;
   if (!ok) {
     *err = "GEMM path: out of device memory for a group of " + std::to_string(cap);
     return EPIE_ECUDA;
@@ -404,7 +447,7 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
-  const bool split_launch = split_precision(g->precision) || g->precision == EPIE_GEMM_TC_TF32X3;
+  const bool split_launch = split_precision(g->precision) || tc_tf32_precision(g->precision);
   // gather, 2 transposes, modulus, update (+ 4 splits, + 4 tcgen05 GEMMs)
   *kernels += 5 + (split_launch ? 4 : 0) + (tc_precision(g->precision) ? 4 : 0);
   return EPIE_OK;
