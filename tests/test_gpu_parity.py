@@ -445,3 +445,26 @@ def test_dark_field_set_after_append_rederives_amplitudes():
                  (("frames",), ("dark", "frames", "clear"))]:
         ra, rb = run(a), run(b)
         assert all(np.array_equal(x, y) for x, y in zip(ra, rb)), (a, b)
+
+
+def test_minibatch_256_with_dark_field(orc):
+    """Mini-batch sweep at 256^2 on 8-CTA clusters with a dark field: the
+    derived-amplitude tiles, the tensor-memory values of the mini-batch
+    branch and the count-normalised object apply, against the oracle."""
+    d = synth.small_scan(256, 2, 3, 130, seed=6, dark=True, photons=1e7)
+    st = textured_start(d)
+    I_all = orc.prepare_intensity(d["frames"], d["dark"])
+    order = orc.order_sequential(5, 0, len(d["pos"]))
+
+    def run(s0):
+        O, P = s0[0].copy(), s0[1].copy()
+        er, ir = orc.sweep_minibatch(O, P, I_all, d["pos"], order, 3)
+        return O, P, np.array([er / ir])
+
+    (O, P, e), sp = spread(run, st)
+    assert max(sp[:2]) <= WELL_CONDITIONED, sp
+    with engine(d, B.EPIE_MINIBATCH, st, batch=3) as eng:
+        eng.set_dark(d["dark"])
+        eng.append(d["frames"], d["pos"])
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
