@@ -363,6 +363,157 @@ def test_minibatch_overlap_count_normalisation(orc):
     assert rel(Oa, Ob) <= 1e-15 and rel(Pa, Pb) <= 1e-15
 
 
+def _flat_batch_instance(N=16, H=40, W=60):
+    """Two disjoint flat patches under a flat probe, with intensities that put
+    A_j^2 at DC and B_j^2 at one other frequency k_j per frame.  Returns the
+    instance and the closed-form replaced exit waves psi1_j (see
+    test_step_closed_form_flat_probe)."""
+    rng = np.random.default_rng(17)
+    c = 0.7 - 0.4j
+    pos = np.array([[3, 2], [5, 2 + N + 9]], np.int32)          # disjoint patches
+    o = [0.3 + 0.9j, -0.6 + 0.2j]
+    A, B = [3.0, 2.2], [1.5, 0.7]
+    k = [(1, 3), (4, 1)]
+    K = N * N
+    O = crandn(rng, (H, W))
+    for (y0, x0), oj in zip(pos, o):
+        O[y0:y0 + N, x0:x0 + N] = oj
+    P = np.full((N, N), c, complex)
+    I_all = np.zeros((2, N, N))
+    y, x = np.mgrid[0:N, 0:N]
+    psi1 = []
+    for j in range(2):
+        I_all[j, 0, 0], I_all[j, k[j][0], k[j][1]] = A[j] ** 2, B[j] ** 2
+        u = c * o[j] / abs(c * o[j])
+        psi1.append((A[j] * u + B[j] * np.exp(2j * math.pi * (k[j][0] * y + k[j][1] * x) / N)) / K)
+    return O, P, I_all, pos, c, o, psi1
+
+
+def test_minibatch_alpha_beta_closed_form(orc):
+    """C5 at alpha = 0.5, beta = 0.3 on a batch of two disjoint flat patches
+    under a flat probe: every pixel is covered once, so each patch moves by
+    alpha conj(c)/|c|^2 d_j and the probe by the mean of beta conj(o_j)/|o_j|^2 d_j.
+    Planted mistakes this catches: alpha applied twice (alpha/max|P|^2 in the
+    accumulator and alpha again when applying it), beta dropped or applied to
+    the object, the probe moved by the sum instead of the mean."""
+    N = 16
+    O, P, I_all, pos, c, o, psi1 = _flat_batch_instance(N)
+    alpha, beta = 0.5, 0.3
+    O1, P1 = O.copy(), P.copy()
+    orc.sweep_minibatch(O1, P1, I_all, pos, np.array([0, 1]), 2, alpha=alpha, beta=beta)
+    O_exp = O.copy()
+    dP = np.zeros((N, N), complex)
+    for j, (y0, x0) in enumerate(pos):
+        d = psi1[j] - c * o[j]
+        O_exp[y0:y0 + N, x0:x0 + N] = o[j] + alpha * np.conj(c) / abs(c) ** 2 * d
+        dP += beta * np.conj(o[j]) / abs(o[j]) ** 2 * d
+    assert np.abs(O1 - O_exp).max() <= 1e-13
+    assert np.abs(P1 - (c + dP / 2)).max() <= 1e-13
+
+
+def test_minibatch_alpha_beta_reductions(orc):
+    """C5 at alpha = 0.5, beta = 0.3: (i) a batch of disjoint patches equals the
+    coloured group update at the same strengths (mean probe move); (ii) two
+    copies of one position in a batch equal that position's single ePIE step
+    (count normalisation and probe mean both undo the duplication).  With
+    alpha applied twice the first part fails; with the count or the mean
+    missing the second does."""
+    N = 16
+    alpha, beta = 0.5, 0.3
+    pos, I_all, O0, P0 = _sparse_instance(N)
+    col, ncls = orc.colour_greedy(pos, N)
+    order, gs = orc.order_coloured(2, 0, col, ncls)
+    kk = int(np.argmax(np.diff(gs)))
+    sub = order[gs[kk]:gs[kk + 1]]
+    assert len(sub) > 1
+    Oa, Pa = O0.copy(), P0.copy()
+    orc.sweep_minibatch(Oa, Pa, I_all, pos, sub, len(sub), alpha=alpha, beta=beta)
+    Ob, Pb = O0.copy(), P0.copy()
+    orc.sweep_groups(Ob, Pb, I_all, pos, sub, np.array([0, len(sub)]), alpha=alpha, beta=beta)
+    assert rel(Oa, Ob) <= 1e-14 and rel(Pa, Pb) <= 1e-14 and rel(Oa, O0) > 1e-3
+    pos2 = np.array([pos[3], pos[3]], np.int32)
+    I2 = np.stack([I_all[3], I_all[3]])
+    Oc, Pc = O0.copy(), P0.copy()
+    orc.sweep_minibatch(Oc, Pc, I2, pos2, np.array([0, 1]), 2, alpha=alpha, beta=beta)
+    O1, P1, _, _ = orc.epie_step(O0, P0, I_all[3], pos[3][0], pos[3][1], alpha, beta)
+    assert rel(Oc, O1) <= 1e-14 and rel(Pc, P1) <= 1e-14
+
+
+def test_probe_sum_closed_form_multi_member(orc):
+    """Coloured group update with probe_mean off (the EPIE_PROBE_SUM reading):
+    a class of two disjoint flat patches under a flat probe moves the probe by
+    the SUM of beta conj(o_j)/|o_j|^2 d_j, and each patch as in the single
+    step.  Planted mistake it catches: the mean taken regardless of the flag
+    (or the flag inverted)."""
+    N = 16
+    O, P, I_all, pos, c, o, psi1 = _flat_batch_instance(N)
+    alpha, beta = 0.8, 0.6
+    O1, P1 = O.copy(), P.copy()
+    orc.sweep_groups(O1, P1, I_all, pos, np.array([0, 1]), np.array([0, 2]), alpha=alpha,
+                     beta=beta, probe_mean=False)
+    O_exp = O.copy()
+    dP = np.zeros((N, N), complex)
+    for j, (y0, x0) in enumerate(pos):
+        d = psi1[j] - c * o[j]
+        O_exp[y0:y0 + N, x0:x0 + N] = o[j] + alpha * np.conj(c) / abs(c) ** 2 * d
+        dP += beta * np.conj(o[j]) / abs(o[j]) ** 2 * d
+    assert np.abs(O1 - O_exp).max() <= 1e-13
+    assert np.abs(P1 - (c + dP)).max() <= 1e-13
+    P2 = P.copy()
+    orc.sweep_groups(O.copy(), P2, I_all, pos, np.array([0, 1]), np.array([0, 2]), alpha=alpha,
+                     beta=beta, probe_mean=True)
+    assert np.abs(P2 - (c + dP / 2)).max() <= 1e-13
+
+
+def test_group_global_object_max_single_members(orc):
+    """omax_global in a sweep of one-member groups equals the chain of single
+    ePIE steps with the global maximum (whose closed form is pinned in
+    test_step_global_object_max).  Catches a group-level global maximum read
+    from the wrong array (the probe, or the patch)."""
+    N = 16
+    pos, I_all, O0, P0 = _sparse_instance(N)
+    O0 = O0 * np.exp(0.3j) * np.linspace(0.5, 1.5, O0.size).reshape(O0.shape)
+    order = orc.order_sequential(3, 0, len(pos))
+    Oa, Pa = O0.copy(), P0.copy()
+    orc.sweep_groups(Oa, Pa, I_all, pos, order, orc.sequential_groups(order), omax_global=True)
+    Ob, Pb = O0.copy(), P0.copy()
+    for j in order:
+        Ob, Pb, _, _ = orc.epie_step(Ob, Pb, I_all[j], pos[j][0], pos[j][1], omax_global=True)
+    assert rel(Oa, Ob) <= 1e-14 and rel(Pa, Pb) <= 1e-14
+    Oc, Pc = O0.copy(), P0.copy()
+    orc.sweep_groups(Oc, Pc, I_all, pos, order, orc.sequential_groups(order))
+    assert rel(Pc, Pa) > 1e-6  # the patch maximum gives another probe
+
+
+def test_group_global_object_max_taken_at_class_start(orc):
+    """omax_global in a class of two disjoint members: the maximum is the
+    object's at class start (reading R4), so each member's probe move equals
+    a single step from the class-start object with the global maximum, and
+    the probe moves by their mean.  The object's largest pixel sits in the
+    first member's patch and that member's update shrinks it, so a maximum
+    re-read after the first member (from the current object) fails here."""
+    N = 16
+    O, P, I_all, pos, c, o, psi1 = _flat_batch_instance(N)
+    y0, x0 = pos[0]
+    O[y0 + 2, x0 + 5] = 4.0 + 3.0j                      # |.|^2 = 25, the global maximum
+    O[:, :] = np.where(np.abs(O) > 5.0, O / np.abs(O) * 4.5, O)
+    O[y0 + 2, x0 + 5] = 4.0 + 3.0j
+    assert np.argmax(np.abs(O)) == (y0 + 2) * O.shape[1] + x0 + 5
+    I_all = I_all.copy()
+    I_all[0] *= 0.01                                    # the update pulls the patch down
+    O1, P1 = O.copy(), P.copy()
+    orc.sweep_groups(O1, P1, I_all, pos, np.array([0, 1]), np.array([0, 2]), omax_global=True)
+    O_exp, dP = O.copy(), np.zeros_like(P)
+    for j, (yy, xx) in enumerate(pos):
+        Oj, Pj, _, _ = orc.epie_step(O, P, I_all[j], yy, xx, omax_global=True)
+        O_exp[yy:yy + N, xx:xx + N] = Oj[yy:yy + N, xx:xx + N]
+        dP += Pj - P
+    assert rel(O1, O_exp) <= 1e-14 and rel(P1, P + dP / 2) <= 1e-14
+    # the teeth: after the first member the object maximum is smaller
+    Oa, _, _, _ = orc.epie_step(O, P, I_all[0], y0, x0, omax_global=True)
+    assert np.max(np.abs(Oa) ** 2) < 0.9 * np.max(np.abs(O) ** 2)
+
+
 # --------------------------------------------------------------------------- order, colouring
 
 def test_splitmix64_golden(orc):
