@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--geometry", default="A", choices=["A", "B"])
     ap.add_argument("--frames", type=int, default=10000)
+    ap.add_argument("--frame-side", type=int, default=256, choices=[64, 128, 256, 512],
+                    help="live workload at another frame side (probe FWHM 60 px x N/256); "
+                         "the headline is 256")
     ap.add_argument("--path", default="fused", choices=["fused", "plain"])
     ap.add_argument("--graph", action="store_true",
                     help="replay each sweep's launches from a captured CUDA graph")
@@ -215,15 +218,17 @@ def replica_rate(units, seconds, device="cpu"):
 def workload(args):
     from paper_2308_10674_gb300 import synth
     t = time.time()
-    d = synth.live_scan(N=256, n=args.frames, geometry=args.geometry, seed=0,
-                        workers=args.workers)
+    N = args.frame_side
+    d = synth.live_scan(N=N, n=args.frames, geometry=args.geometry, seed=0,
+                        workers=args.workers, fwhm=60.0 * N / 256)
     d["gen_s"] = time.time() - t
     return d
 
 
 def workload_name(args, d):
-    return (f"live ePIE 256^2 uint16, {args.frames} Fermat-spiral positions (step 0.35 FWHM, "
-            f"FWHM 60 px), object {d['H']}x{d['W']} c64, 1e8 photons + Poisson + 2% dark, "
+    N = d["N"]
+    return (f"live ePIE {N}^2 uint16, {args.frames} Fermat-spiral positions (step 0.35 FWHM, "
+            f"FWHM {60 * N // 256} px), object {d['H']}x{d['W']} c64, 1e8 photons + Poisson + 2% dark, "
             f"coloured, chunks of {CHUNK}")
 
 
@@ -399,7 +404,7 @@ def run_ours(args):
     achieved = flops_per_launch / (kernel_avg_ms / 1e3) / 1e12
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    tr = measured_traffic()
+    tr = measured_traffic() if N == 256 else None
     traffic = None if tr is None else tr["dram_bytes_per_frame"] * frames_per_launch
     hbm_bytes_per_frame = N * N * 4  # the frame's fp32 measured-amplitude tile
     hbm_achieved = hbm_bytes_per_frame * frames_per_launch / (kernel_avg_ms / 1e3) / 1e9
@@ -412,7 +417,7 @@ def run_ours(args):
         fma = {"unavailable": str(ex)}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                 "frac": achieved / peak_fp32, "traffic": traffic,
-                "kernel": "epie_fused_kernel<256,8,512,u16>",
+                "kernel": f"epie_fused_kernel<{N},...>",
                 "flops_per_frame": fft_flops(N), "frames_per_launch": frames_per_launch,
                 "avg_launch_ms": kernel_avg_ms, "launches": k_launches,
                 "peak_note": (f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 "

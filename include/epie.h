@@ -245,9 +245,37 @@ EPIE_API int epie_get_order(epie_t h, int64_t sweep, int32_t *order, int32_t *gr
 EPIE_API int epie_get_sweep_index(epie_t h, int64_t *sweep);
 EPIE_API int epie_set_sweep_index(epie_t h, int64_t sweep);
 
+/* Frame count of each sweep of the most recent epie_iterate call on this
+ * handle: the size of the frame set the sweep snapshotted when it started
+ * (paper, Sec. "Live ePIE": frames appended by another thread join at the
+ * next sweep).  *n_out receives the number of sweeps that call ran; the
+ * first min(*n_out, cap) counts go to `counts` (host).  Callable while
+ * another thread iterates (it takes the handle's mutex between sweeps).
+ * EPIE_EINVAL for a NULL handle or output. */
+EPIE_API int epie_last_sweep_frames(epie_t h, int32_t *counts, int32_t cap, int32_t *n_out);
+
 /* Device time of the last epie_iterate call in milliseconds (CUDA events on
  * the handle's stream) and the number of kernels it launched. */
 EPIE_API int epie_last_timing(epie_t h, double *ms, int64_t *kernels);
+
+/* Failure injection for the tests of the bounded device waits.  No GPU
+ * fault is involved: a bulk copy that is never issued leaves its mbarrier
+ * incomplete, the wait for it expires after wait_ns, the kernel sets its
+ * status word, lets everything it did issue land, frees its tensor memory
+ * and returns; the host turns the status into EPIE_ETIMEOUT.
+ *   what = EPIE_INJECT_STEP_COPY: the next `count` launches of the fused
+ *          step kernel of handle h (fused path, EPIE_GRAPH off) skip the
+ *          intensity-tile copy on their first CTA; epie_iterate then
+ *          returns EPIE_ETIMEOUT and the handle is unusable (EPIE_ESTATE);
+ *   what = EPIE_INJECT_TC_COPY: the next `count` calls of the tcgen05 GEMM
+ *          (epie_tc_gemm_bf16 / _tf32, or the GEMM path) skip the first
+ *          operand copy on CTA 0 and set FLAG bit 2 of their status word
+ *          (h may be NULL; process-wide).
+ * wait_ns in [1e3, 2e9] bounds every wait of the injected launches (the
+ * default limit is 2 s).  Returns EPIE_EINVAL for other arguments. */
+#define EPIE_INJECT_STEP_COPY 1
+#define EPIE_INJECT_TC_COPY 2
+EPIE_API int epie_inject_fault(epie_t h, int32_t what, int32_t count, int64_t wait_ns);
 
 /* Total number of kernels this handle has launched since epie_init (all
  * calls: ingest, step, reductions; library calls such as cuFFT excluded). */
@@ -282,8 +310,14 @@ EPIE_API int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t
  *            pairwise disjoint when n_members > 1
  *   dark     device, N*N float32 in FFT order, or NULL
  *   err_terms host, 2 doubles receiving sum (|Psi| - sqrt I)^2 and sum I over
- *            the group, or NULL; when given, the call waits for the step
+ *            the group, or NULL
  *   stream   cudaStream_t (NULL: the legacy default stream)
+ * Alignment: frames and probe 16-byte aligned, object 8-byte, pos, members
+ * and dark 4-byte; a misaligned pointer gives EPIE_EINVAL before any launch.
+ * Every call synchronises `stream` twice: once to read the device-side
+ * validation of members and positions before the step, and once at the end
+ * to read the step kernel's status word, so an expired bounded wait always
+ * returns EPIE_ETIMEOUT (err_terms given or not).
  * All scratch lives in one file-scope device array of about 36 MiB that every
  * GPU loading the library holds until exit; calls share it and it keeps the
  * last call's contents, so calls that overlap on the GPU (other streams,
@@ -292,8 +326,9 @@ EPIE_API int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t
  * call returns EPIE_EINVAL without launching anything.  Member ids,
  * positions and disjointness are checked on the device before the step
  * (EPIE_EINVAL / EPIE_ERANGE).  The first call on a device looks the array's
- * device address up and uploads the twiddle tables; make that first call
- * before any stream capture.  On failure epie_error(NULL) holds the reason. */
+ * device address up, uploads the twiddle tables and waits for the device to
+ * finish that upload; make that first call before any stream capture begins.
+ * On failure epie_error(NULL) holds the reason. */
 EPIE_API int epie_group_step_static(int32_t N, int32_t intensity_dtype, float *object,
                                     int32_t obj_h, int32_t obj_w, float *probe,
                                     const void *frames, int32_t n_frames, const int32_t *pos,

@@ -83,6 +83,8 @@ def lib():
         L.epie_get_sweep_index.argtypes = [H, C.POINTER(i64)]
         L.epie_set_sweep_index.argtypes = [H, i64]
         L.epie_last_timing.argtypes = [H, C.POINTER(C.c_double), C.POINTER(i64)]
+        L.epie_last_sweep_frames.argtypes = [H, vp, i32, C.POINTER(i32)]
+        L.epie_inject_fault.argtypes = [H, i32, i32, i64]
         L.epie_launch_count.argtypes = [H, C.POINTER(i64)]
         L.epie_set_kernel_timing.argtypes = [H, i32]
         L.epie_kernel_timing.argtypes = [H, C.POINTER(i64), C.POINTER(C.c_double),
@@ -263,6 +265,15 @@ def epie_last_timing(h):
     return ms.value, k.value
 
 
+def epie_last_sweep_frames(h):
+    """Frame counts of the sweeps of the most recent epie_iterate call."""
+    n = C.c_int32()
+    _check(h, lib().epie_last_sweep_frames(h, None, 0, C.byref(n)))
+    out = np.zeros(n.value, np.int32)
+    _check(h, lib().epie_last_sweep_frames(h, _p(out), n.value, C.byref(n)))
+    return out[:n.value]
+
+
 def epie_launch_count(h):
     n = C.c_int64()
     _check(h, lib().epie_launch_count(h, C.byref(n)))
@@ -314,6 +325,19 @@ def epie_tc_gemm_bf16(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, status, stream=No
                                  v(status), v(stream))
     if rc != EPIE_OK:
         raise EpieError(rc, epie_error(None))
+
+
+EPIE_INJECT_STEP_COPY, EPIE_INJECT_TC_COPY = 1, 2
+
+
+def epie_inject_fault(h, what, count, wait_ns):
+    """Failure injection for the timeout tests: the next `count` launches of
+    the step kernel (what = EPIE_INJECT_STEP_COPY, handle h) or of the tcgen05
+    GEMM (EPIE_INJECT_TC_COPY, h may be None) skip one bulk copy, and their
+    waits give up after wait_ns."""
+    rc = lib().epie_inject_fault(h, what, count, wait_ns)
+    if rc != EPIE_OK:
+        raise EpieError(rc, epie_error(h))
 
 
 def epie_fp32_fma_peak(device=0, iters=4096):
@@ -431,3 +455,6 @@ class Engine:
 
     def last_timing(self):
         return epie_last_timing(self.h)
+
+    def last_sweep_frames(self):
+        return epie_last_sweep_frames(self.h)

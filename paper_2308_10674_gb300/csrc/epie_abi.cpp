@@ -21,6 +21,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/epie.h"
@@ -64,6 +65,7 @@ std::string &init_error_sink() { return g_init_error; }
 
 struct epie_ctx {
   std::mutex mu;
+  std::atomic<int> waiting{0};  // calls blocked on mu (epie_iterate yields to them)
   epie_config cfg{};
   std::string err;
   bool dead = false;
@@ -73,6 +75,7 @@ struct epie_ctx {
   cudaStream_t up = nullptr;    // upload stream (appends)
   bool own_stream = false;
   cudaEvent_t ev_up = nullptr;  // last upload finished
+  cudaEvent_t ev_st = nullptr;  // work queued on st so far (appends wait for it)
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
   double last_ms = 0.0;
   int64_t last_kernels = 0;
@@ -144,6 +147,10 @@ struct epie_ctx {
   int cell_rows = 0, cell_cols = 0;
   std::vector<uint32_t> stamp;          // per class: last frame that marked it
   int64_t sweep = 0;
+  std::vector<int32_t> iter_frames;     // frames of each sweep of the last epie_iterate
+  // failure injection (epie_inject_fault): step launches still to inject, wait limit
+  int inject_steps = 0;
+  unsigned long long inject_wait_ns = 0;
 
   int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -167,6 +174,24 @@ struct epie_ctx {
   } while (0)
 
 namespace {
+
+// The handle's mutex for one call.  The caller is counted while it waits,
+// so that a thread in epie_iterate lets it in at the next sweep boundary
+// (a plain mutex would let the iterating thread re-take it at once).
+class CallLock {
+ public:
+  explicit CallLock(epie_ctx *h) : h_(h) {
+    h_->waiting.fetch_add(1);
+    h_->mu.lock();
+    h_->waiting.fetch_sub(1);
+  }
+  ~CallLock() { h_->mu.unlock(); }
+  CallLock(const CallLock &) = delete;
+  CallLock &operator=(const CallLock &) = delete;
+
+ private:
+  epie_ctx *h_;
+};
 
 int check_handle(epie_t h) {
   if (!h) return EPIE_EINVAL;
@@ -319,6 +344,11 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, bool o_early
     CK(cudaEventRecord(h->kev[h->kev_used], h->st));
   }
   if (h->cfg.path == EPIE_PATH_FUSED) {
+    if (h->inject_steps > 0) {
+      --h->inject_steps;
+      a.inject_skip_copy = 1;
+      a.wait_ns = h->inject_wait_ns;
+    }
     CK(epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st));
     *kernels += 1;
   } else if (h->cfg.path == EPIE_PATH_GEMM) {
@@ -546,7 +576,7 @@ const char *epie_error(epie_t h) { return h ? h->err.c_str() : g_init_error.c_st
 int epie_destroy(epie_t h) {
   if (!h) return EPIE_OK;
   {
-    std::lock_guard<std::mutex> lk(h->mu);
+    CallLock lk(h);
     cudaSetDevice(h->cfg.device);
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->up) cudaStreamSynchronize(h->up);
@@ -568,7 +598,7 @@ int epie_destroy(epie_t h) {
     for (void *p : h->stage_h)
       if (p) cudaFreeHost(p);
     if (h->err_h) cudaFreeHost(h->err_h);
-    for (cudaEvent_t e : {h->ev_up, h->ev_t0, h->ev_t1, h->ev_stage[0], h->ev_stage[1]})
+    for (cudaEvent_t e : {h->ev_up, h->ev_st, h->ev_t0, h->ev_t1, h->ev_stage[0], h->ev_stage[1]})
       if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : h->kev) cudaEventDestroy(e);
     if (h->up) cudaStreamDestroy(h->up);
@@ -655,6 +685,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   }
   IK(cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking));
   IK(cudaEventCreateWithFlags(&h->ev_up, cudaEventDisableTiming));
+  IK(cudaEventCreateWithFlags(&h->ev_st, cudaEventDisableTiming));
   IK(cudaEventCreate(&h->ev_t0));
   IK(cudaEventCreate(&h->ev_t1));
   IK(cudaEventCreateWithFlags(&h->ev_stage[0], cudaEventDisableTiming));
@@ -747,7 +778,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
 int epie_set_dark(epie_t h, const float *dark) {
   int rc = check_handle(h);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   CK(cudaSetDevice(h->cfg.device));
   CK(cudaStreamWaitEvent(h->st, h->ev_up, 0));
   if (dark) {
@@ -773,7 +804,7 @@ int epie_set_dark(epie_t h, const float *dark) {
 static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t n, bool device) {
   int rc = check_handle(h);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (n < 0 || (n > 0 && (!frames || !pos))) return h->fail(EPIE_EINVAL, "append: bad arguments");
   if (n == 0) return EPIE_OK;
   const int N = h->cfg.N;
@@ -787,6 +818,11 @@ static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t
                      x, h->cfg.obj_h, h->cfg.obj_w);
   }
   CK(cudaSetDevice(h->cfg.device));
+  // Sweeps queued on st may still read the slots this append writes (after
+  // a truncation, the frames and positions past n_keep): the upload stream
+  // waits for everything queued on st so far.
+  CK(cudaEventRecord(h->ev_st, h->st));
+  CK(cudaStreamWaitEvent(h->up, h->ev_st, 0));
   const size_t es = esize_of(h->cfg.intensity_dtype);
   const size_t fb = es * h->K;
   const int per = static_cast<int>(h->stage_bytes / fb);
@@ -854,7 +890,7 @@ int epie_append_frames_device(epie_t h, const void *frames_dev, const int32_t *p
 int epie_truncate_frames(epie_t h, int32_t n_keep) {
   int rc = check_handle(h);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (n_keep < 0 || n_keep > h->n_frames)
     return h->fail(EPIE_EINVAL, "truncate: n_keep %d outside [0, %d]", n_keep, h->n_frames);
   const int N = h->cfg.N;
@@ -915,7 +951,7 @@ int epie_iterate_many(epie_t *hs, int32_t k, int32_t n_sweeps, double *err) {
       for (int32_t i = 0; i < k; ++i) {
         if (failed[i]) continue;
         epie_t h = hs[i];
-        std::lock_guard<std::mutex> lk(h->mu);
+        CallLock lk(h);
         int64_t kern = 0;
         int rc = cudaSetDevice(h->cfg.device) == cudaSuccess ? EPIE_OK
                                                              : h->fail(EPIE_ECUDA, "cudaSetDevice");
@@ -932,7 +968,7 @@ int epie_iterate_many(epie_t *hs, int32_t k, int32_t n_sweeps, double *err) {
     for (int32_t i = 0; i < k; ++i) {
       if (failed[i]) continue;
       epie_t h = hs[i];
-      std::lock_guard<std::mutex> lk(h->mu);
+      CallLock lk(h);
       int rc = fetch_errors(h, 0, cn, c0, err ? err + static_cast<size_t>(i) * n_sweeps : nullptr);
       if (rc) {
         failed[i] = 1;
@@ -1001,11 +1037,17 @@ int epie_iterate(epie_t h, int32_t n_sweeps, double *err_per_sweep) {
     std::lock_guard<std::mutex> lk(h->mu);
     CK(cudaSetDevice(h->cfg.device));
     CK(cudaEventRecord(h->ev_t0, h->st));
+    h->iter_frames.clear();
   }
   for (int32_t s = 0; s < n_sweeps; ++s) {
-    std::lock_guard<std::mutex> lk(h->mu);  // appends may slip in between sweeps
+    // Calls from other threads (a feeder's append) slip in between sweeps:
+    // while one is waiting for the mutex, hand it over instead of re-taking
+    // it at once (bounded, so a stream of calls cannot stall the sweeps).
+    for (int spin = 0; h->waiting.load() > 0 && spin < 100000; ++spin) std::this_thread::yield();
+    std::lock_guard<std::mutex> lk(h->mu);
     if (h->dead) return h->fail(EPIE_ESTATE, "handle unusable: %s", h->err.c_str());
     const int slot = s % 1024;
+    h->iter_frames.push_back(h->n_frames);
     rc = run_sweep(h, slot, &kernels);
     if (rc) return rc;
     h->sweep += 1;
@@ -1056,7 +1098,7 @@ static int copy_state(epie_t h, void *host, const void *dev, size_t bytes, size_
                       size_t n_floats, bool to_dev, const char *what) {
   int rc = check_handle(h);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (!host || n_floats != want_floats)
     return h->fail(EPIE_EINVAL, "%s: need %zu floats, got %zu", what, want_floats, n_floats);
   CK(cudaSetDevice(h->cfg.device));
@@ -1092,7 +1134,7 @@ int epie_set_probe(epie_t h, const float *src, size_t n_floats) {
   int rc = copy_state(h, const_cast<float *>(src), h->P, sizeof(float2) * h->K,
                       2 * static_cast<size_t>(h->K), n_floats, true, "set_probe");
   if (rc) return rc;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if ((rc = recompute_pmax(h))) return rc;
   CK(cudaStreamSynchronize(h->st));
   return EPIE_OK;
@@ -1100,21 +1142,21 @@ int epie_set_probe(epie_t h, const float *src, size_t n_floats) {
 
 int epie_num_frames(epie_t h, int32_t *n) {
   if (!h || !n) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   *n = h->n_frames;
   return EPIE_OK;
 }
 
 int epie_num_classes(epie_t h, int32_t *n) {
   if (!h || !n) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   *n = static_cast<int32_t>(h->classes.size());
   return EPIE_OK;
 }
 
 int epie_get_colours(epie_t h, int32_t *colour, int32_t n) {
   if (!h || (!colour && n > 0)) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (n < 0 || n > h->n_frames) return h->fail(EPIE_EINVAL, "get_colours: bad count %d", n);
   std::copy(h->colour.begin(), h->colour.begin() + n, colour);
   return EPIE_OK;
@@ -1123,7 +1165,7 @@ int epie_get_colours(epie_t h, int32_t *colour, int32_t n) {
 int epie_get_order(epie_t h, int64_t sweep, int32_t *order, int32_t *group_start,
                    int32_t *n_groups) {
   if (!h || !n_groups) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (h->n_frames > 0 && (!order || !group_start))
     return h->fail(EPIE_EINVAL, "get_order: NULL output");
   std::vector<int32_t> o, g;
@@ -1136,21 +1178,21 @@ int epie_get_order(epie_t h, int64_t sweep, int32_t *order, int32_t *group_start
 
 int epie_get_sweep_index(epie_t h, int64_t *sweep) {
   if (!h || !sweep) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   *sweep = h->sweep;
   return EPIE_OK;
 }
 
 int epie_set_sweep_index(epie_t h, int64_t sweep) {
   if (!h || sweep < 0) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   h->sweep = sweep;
   return EPIE_OK;
 }
 
 int epie_last_timing(epie_t h, double *ms, int64_t *kernels) {
   if (!h) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (ms) *ms = h->last_ms;
   if (kernels) *kernels = h->last_kernels;
   return EPIE_OK;
@@ -1203,16 +1245,47 @@ int epie_fp32_fma_peak(int32_t device, int32_t iters, double *tflops, double *sm
   return rc;
 }
 
+int epie_last_sweep_frames(epie_t h, int32_t *counts, int32_t cap, int32_t *n_out) {
+  if (!h || !n_out || cap < 0 || (cap > 0 && !counts)) return EPIE_EINVAL;
+  CallLock lk(h);
+  const int32_t n = static_cast<int32_t>(h->iter_frames.size());
+  *n_out = n;
+  for (int32_t i = 0; i < std::min(n, cap); ++i) counts[i] = h->iter_frames[i];
+  return EPIE_OK;
+}
+
+int epie_inject_fault(epie_t h, int32_t what, int32_t count, int64_t wait_ns) {
+  if (count < 0 || wait_ns < 1000 || wait_ns > 2000000000LL) {
+    g_init_error = "epie_inject_fault: count >= 0 and wait_ns in [1e3, 2e9] required";
+    return EPIE_EINVAL;
+  }
+  if (what == EPIE_INJECT_TC_COPY) {
+    epie::tc_gemm_inject(count, wait_ns);
+    return EPIE_OK;
+  }
+  if (what != EPIE_INJECT_STEP_COPY || !h) {
+    g_init_error = "epie_inject_fault: unknown kind, or no handle for EPIE_INJECT_STEP_COPY";
+    return EPIE_EINVAL;
+  }
+  CallLock lk(h);
+  if (h->cfg.path != EPIE_PATH_FUSED || (h->cfg.flags & EPIE_GRAPH))
+    return h->fail(EPIE_EINVAL, "epie_inject_fault: step injection needs the fused path without "
+                                "EPIE_GRAPH");
+  h->inject_steps = count;
+  h->inject_wait_ns = static_cast<unsigned long long>(wait_ns);
+  return EPIE_OK;
+}
+
 int epie_launch_count(epie_t h, int64_t *total) {
   if (!h || !total) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   *total = h->launches_total;
   return EPIE_OK;
 }
 
 int epie_set_kernel_timing(epie_t h, int32_t on) {
   if (!h) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   h->ktime = on != 0;
   h->kev_used = 0;
   return EPIE_OK;
@@ -1220,7 +1293,7 @@ int epie_set_kernel_timing(epie_t h, int32_t on) {
 
 int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t *frames) {
   if (!h) return EPIE_EINVAL;
-  std::lock_guard<std::mutex> lk(h->mu);
+  CallLock lk(h);
   if (launches) *launches = h->kt_launches;
   if (ms) *ms = h->kt_ms;
   if (frames) *frames = h->kt_frames;

@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   // this thread's columns: [0, 32) object patch, [32, 64) probe
   const uint32_t tm = tm_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
                       static_cast<uint32_t>((warp >> 2) * 64);
-  if (tid == 0) {
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
+  // (failure injection: the launch's first CTA never issues its copy)
+  if (tid == 0 && !(a.inject_skip_copy && blockIdx.x == 0)) {
     // the frame is read once per sweep: keep it from evicting the object.
     // With derived amplitudes the tile arrives ready for the modulus.
     if (a.amp) {
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   }
 
   // ---------------------------------------------------------------- phase 2
-  bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+  bool ok = mbar_wait_bounded(bar, 0, wait_ns);
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
   ok = __all_sync(0xffffffffu, ok);  // warp-uniform: phase 3 reads TMEM warp-collectively
   float isum_t = 0.f;  // sum I of this thread's tile elements
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     }
   } else {
     // the copy never arrived: give it one more bounded wait before exiting
-    mbar_wait_bounded(bar, 0, 100000000ull);
+    mbar_wait_bounded(bar, 0, wait_ns < 100000000ull ? wait_ns : 100000000ull);
   }
 #undef EPIE_LD_O
 #undef EPIE_ST_O

@@ -61,6 +61,11 @@ struct GroupArgs {
   // kernel copies its amplitude tile instead of converting raw intensities
   const float *amp;
   const double *amp_isum;
+  // limit of every bounded device wait (0: the default of 2 s), and the
+  // failure injection of the timeout tests: when set, the first CTA of the
+  // launch never issues its intensity-tile copy, so its wait expires
+  unsigned long long wait_ns;
+  int inject_skip_copy;
 };
 
 // error-flag bits written by kernels
@@ -122,6 +127,10 @@ cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
                                  const double *omax2, float2 *accO, int *cnt, cudaStream_t st);
 cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
                             cudaStream_t st);
+
+// failure injection for the timeout tests: the next `count` tcgen05 GEMM
+// calls skip the first operand copy on CTA 0 and bound their waits by wait_ns
+void tc_gemm_inject(int count, long long wait_ns);
 
 // tensor-core DFT path (epie_gemm.cu)
 // D[M x Nn] = sum_t A_t B_t^T on the tensor cores (tcgen05, epie_tc_gemm.cu);

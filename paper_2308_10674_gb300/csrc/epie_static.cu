@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -133,6 +134,12 @@ int setup_device(int dev, unsigned char **base) {
     e = cudaMemcpy(d.base + kOffTw, tw, kTwBytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
       return fail(EPIE_ECUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));
+    // a copy from pageable memory may return before its DMA lands: wait for
+    // it here, so that a first call on a non-blocking stream never reads the
+    // tables early
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+      return fail(EPIE_ECUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));
     d.ready = true;
   }
   *base = d.base;
@@ -170,6 +177,17 @@ extern "C" int epie_group_step_static(int32_t N, int32_t intensity_dtype, float 
                                  "] for N = " + std::to_string(N) + " (static scratch limit)");
   if (!std::isfinite(alpha) || !std::isfinite(beta))
     return fail(EPIE_EINVAL, "alpha and beta must be finite");
+  // the step kernel copies frame rows with bulk copies (16-byte aligned
+  // source), reads the object as float2 and the probe reduction reads and
+  // writes the probe as float4
+  auto misaligned = [](const void *p, uintptr_t a) {
+    return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0;
+  };
+  if (misaligned(frames, 16)) return fail(EPIE_EINVAL, "frames must be 16-byte aligned");
+  if (misaligned(probe, 16)) return fail(EPIE_EINVAL, "probe must be 16-byte aligned");
+  if (misaligned(object, 8)) return fail(EPIE_EINVAL, "object must be 8-byte aligned");
+  if (misaligned(pos, 4) || misaligned(members, 4) || (dark && misaligned(dark, 4)))
+    return fail(EPIE_EINVAL, "pos, members and dark must be 4-byte aligned");
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return fail(EPIE_ECUDA, cudaGetErrorString(ce));
@@ -226,15 +244,19 @@ extern "C" int epie_group_step_static(int32_t N, int32_t intensity_dtype, float 
   SK(epie::launch_fused(N, intensity_dtype, a, st));
   const float scale = probe_mean ? 1.0f / static_cast<float>(n_members) : 1.0f;
   SK(epie::launch_probe_reduce(P, a.probe_part, n_members, N, scale, pmax + 1, st));
+  double h2[2] = {0.0, 0.0};
   if (err_terms) {
     group_error_kernel<<<1, 256, 0, st>>>(a.err_part, a.isum_part, members, n_members,
                                           a.err_stride, gerr);
     SK(cudaGetLastError());
-    double h2[2] = {0.0, 0.0};
     SK(cudaMemcpyAsync(h2, gerr, sizeof h2, cudaMemcpyDeviceToHost, st));
-    SK(cudaMemcpyAsync(&hflag, kflag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SK(cudaStreamSynchronize(st));
-    if (hflag & epie::FLAG_TMA_TIMEOUT) return fail(EPIE_ETIMEOUT, "a bounded device wait expired");
+  }
+  // the kernel status word is read back on every call, so an expired bounded
+  // wait is always reported (the next call clears the word)
+  SK(cudaMemcpyAsync(&hflag, kflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK(cudaStreamSynchronize(st));
+  if (hflag & epie::FLAG_TMA_TIMEOUT) return fail(EPIE_ETIMEOUT, "a bounded device wait expired");
+  if (err_terms) {
     err_terms[0] = h2[0];
     err_terms[1] = h2[1];
   }

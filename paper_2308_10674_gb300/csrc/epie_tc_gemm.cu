@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 
@@ -54,6 +55,9 @@ struct TcElem {
   static constexpr int BK = 128 / BYTES;
 };
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+// failure injection for the tests of the bounded waits (tc_gemm_inject)
+std::atomic<int> g_tc_inject{0};
+std::atomic<long long> g_tc_inject_wait_ns{0};
 
 // ---------------------------------------------------------------- PTX wrappers
 
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                    float *__restrict__ D, int ldd, int K, int terms, int m_tiles, int n_tiles,
-                   int *err_flag) {
+                   int *err_flag, uint64_t wait_ns, int inject) {
   using C = TcCfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   // 128-byte-swizzled tiles want 1024-byte alignment
@@ -215,11 +219,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int m0 = (tile / n_tiles) * TC_BM, n0 = (tile % n_tiles) * BN;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % TC_STAGES, u = it / TC_STAGES;
-          if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], (u - 1) & 1, TC_WAIT_NS)) {
+          if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], (u - 1) & 1, wait_ns)) {
             fail();
             break;
           }
           if (*abort_word) break;
+          if (inject && blockIdx.x == 0 && it == 0) {
+            // failure injection (tests of the timeout path): the first stage's
+            // copies are never issued, so nothing is in flight for it and every
+            // wait on it expires after wait_ns
+            ++it;
+            continue;
+          }
           const int t = kb / kb_term, kx = (kb % kb_term) * BK;
           const CUtensorMap *ma = t == 2 ? &mA1 : &mA0;  // terms: A0 B0, A0 B1, A1 B0
           const CUtensorMap *mb = t == 1 ? &mB1 : &mB0;
@@ -232,7 +243,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // every issued copy has landed before the CTA can exit
       for (int j = it - TC_STAGES < 0 ? 0 : it - TC_STAGES; j < it; ++j)
-        if (!mbar_wait_bounded(&full[j % TC_STAGES], (j / TC_STAGES) & 1, TC_WAIT_NS)) fail();
+        if (!mbar_wait_bounded(&full[j % TC_STAGES], (j / TC_STAGES) & 1, wait_ns)) fail();
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -242,7 +253,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
         if (*abort_word) break;
         const int b = tl & 1, ub = tl >> 1;
-        if (tl >= 2 && !mbar_wait_bounded(&acc_empty[b], (ub - 1) & 1, TC_WAIT_NS)) {
+        if (tl >= 2 && !mbar_wait_bounded(&acc_empty[b], (ub - 1) & 1, wait_ns)) {
           fail();
           break;
         }
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool bad = false;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % TC_STAGES, u = it / TC_STAGES;
-          if (!mbar_wait_bounded(&full[s], u & 1, TC_WAIT_NS)) {
+          if (!mbar_wait_bounded(&full[s], u & 1, wait_ns)) {
             fail();
             bad = true;
             break;
@@ -270,7 +281,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // every issued MMA has finished before the teardown frees the TMEM
       umma_commit(mma_done);
-      if (!mbar_wait_bounded(mma_done, 0, TC_WAIT_NS)) fail();
+      if (!mbar_wait_bounded(mma_done, 0, wait_ns)) fail();
     }
   } else {
     // ---- epilogue: TMEM -> registers -> global; warp w reads TMEM lanes
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int tl = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
       const int b = tl & 1, ub = tl >> 1;
-      bool ok = mbar_wait_bounded(&acc_full[b], ub & 1, TC_WAIT_NS);
+      bool ok = mbar_wait_bounded(&acc_full[b], ub & 1, wait_ns);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok || *abort_word) {
         if (!ok && lane == 0) fail();
@@ -372,7 +383,7 @@ bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_r
 template <int BN, bool TF32>
 cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                       const CUtensorMap &b1, float *D, long long M, int Nn, int K, int ldd,
-                      int terms, int *err_flag, cudaStream_t st) {
+                      int terms, int *err_flag, uint64_t wait_ns, int inject, cudaStream_t st) {
   using C = TcCfg<BN>;
   static int attr_dev = -1, sms = 0;
   int dev = 0;
@@ -389,7 +400,8 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
   const long long tiles = static_cast<long long>(m_tiles) * n_tiles;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);  // one CTA per SM
   tc_gemm_kernel<BN, TF32><<<grid, TC_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms,
-                                                                m_tiles, n_tiles, err_flag);
+                                                                m_tiles, n_tiles, err_flag, wait_ns,
+                                                                inject);
   return cudaGetLastError();
 }
 
@@ -420,13 +432,21 @@ int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, floa
       !make_map(&a1, A1 ? A1 : A0, M, K, TC_BM, tf32, err) ||
       !make_map(&b0, B0, Nn, K, BN, tf32, err) || !make_map(&b1, B1 ? B1 : B0, Nn, K, BN, tf32, err))
     return EPIE_ECUDA;
+  uint64_t w = TC_WAIT_NS;
+  int inj = 0;
+  for (int c = g_tc_inject.load(); c > 0;)
+    if (g_tc_inject.compare_exchange_weak(c, c - 1)) {
+      inj = 1;
+      w = static_cast<uint64_t>(g_tc_inject_wait_ns.load());
+      break;
+    }
   cudaError_t e;
   if (tf32)
-    e = BN == 256 ? launch_tc<256, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
-                  : launch_tc<128, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
+    e = BN == 256 ? launch_tc<256, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st)
+                  : launch_tc<128, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st);
   else
-    e = BN == 256 ? launch_tc<256, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st)
-                  : launch_tc<128, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, st);
+    e = BN == 256 ? launch_tc<256, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st)
+                  : launch_tc<128, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st);
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
@@ -435,6 +455,11 @@ int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, floa
 }
 
 }  // namespace
+
+void tc_gemm_inject(int count, long long wait_ns) {
+  g_tc_inject_wait_ns.store(wait_ns);
+  g_tc_inject.store(count);
+}
 
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,

@@ -17,6 +17,8 @@ oracle itself (tests/test_conditioning.py pins this).
 Integer work (colour classes, visiting orders) is compared bit for bit, and
 two engine runs on the same inputs are bit-identical (fixed-order reductions).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -27,6 +29,13 @@ pytestmark = pytest.mark.gpu
 
 TOL_STATE = 1e-5
 TOL_ERR = 1e-6
+# increments X - X0 of a sharp test (one sweep, or a few short chained ones,
+# from a textured start): the FP32 transforms round at about
+# u log2(N^2) |psi| with u = 6e-8, and a sweep moves the state by 1-10% of
+# its size, so the increment carries a relative error of up to ~2e-5; 1e-4
+# leaves a margin of about 5 (the values the suite reports are in the design
+# notes)
+TOL_INC = 1e-4
 WELL_CONDITIONED = 1e-6
 
 
@@ -80,10 +89,25 @@ def spread(run, start, eps=1e-7, samples=2):
     return (O, P, e), out
 
 
-def assert_parity(O_g, P_g, e_g, O, P, e, tol=TOL_STATE, tol_e=TOL_ERR):
+def increment_errors(O_g, P_g, O, P, start):
+    """Relative L2 error of what the run changed: (X_gpu - X0) against
+    (X_ref - X0) for X in {O, P}, X0 the start state."""
+    O0, P0 = start
+    return rel(np.asarray(O_g) - O0, O - O0), rel(np.asarray(P_g) - P0, P - P0)
+
+
+def assert_parity(O_g, P_g, e_g, O, P, e, tol=TOL_STATE, tol_e=TOL_ERR, start=None,
+                  tol_inc=TOL_INC):
+    """State parity (relative L2 on O, P and the sweep errors) and, given the
+    start state, parity of the increments X - X0 that the sweeps produced."""
     ro, rp = rel(O_g, O), rel(P_g, P)
     re = float(np.max(np.abs(np.asarray(e_g) - e) / np.abs(e)))
+    inc = increment_errors(O_g, P_g, O, P, start) if start is not None else (0.0, 0.0)
+    if os.environ.get("EPIE_PARITY_REPORT"):
+        print(f"parity state O {ro:.2e} P {rp:.2e} E {re:.2e} increment O {inc[0]:.2e} "
+              f"P {inc[1]:.2e}")
     assert ro <= tol and rp <= tol and re <= tol_e, (ro, rp, re)
+    assert inc[0] <= tol_inc and inc[1] <= tol_inc, ("increment", inc)
 
 
 def sharp(orc, d, mode, start, n_sweeps=1, seed=5, **kw):
@@ -108,7 +132,7 @@ def test_sequential_short_chain_sharp(orc):
         assert np.array_equal(order, orc.order_sequential(5, 0, 16))
         assert np.array_equal(gs, np.arange(17))
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 @pytest.mark.parametrize("n_sweeps", [1, 10])
@@ -164,7 +188,7 @@ def test_coloured_one_sweep(orc, N, ny, nx, step, path):
         assert np.array_equal(order, o_ref) and np.array_equal(gs, gs_ref)
         assert ncls > 1 and np.diff(gs).max() > 1
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 def test_coloured_with_class_cap(orc):
@@ -179,7 +203,7 @@ def test_coloured_with_class_cap(orc):
         assert np.array_equal(eng.colours(), col) and eng.n_classes == ncls
         assert np.bincount(col).max() == 3
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 @pytest.mark.parametrize("N", [64, 256])
@@ -190,7 +214,7 @@ def test_sequential_plain_path(orc, N):
     with engine(d, B.EPIE_SEQUENTIAL, st, path=B.EPIE_PATH_PLAIN) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 # --------------------------------------------------------------------------- intensity types, dark field
@@ -203,7 +227,7 @@ def test_intensity_types(orc, dtype, code):
     with engine(d, B.EPIE_COLOURED, st, intensity_dtype=code) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 @pytest.mark.parametrize("path", [B.EPIE_PATH_FUSED, B.EPIE_PATH_PLAIN])
@@ -215,7 +239,7 @@ def test_dark_field(orc, path):
         eng.set_dark(d["dark"])
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 # --------------------------------------------------------------------------- update variants
@@ -227,7 +251,7 @@ def test_global_object_max(orc):
     with engine(d, B.EPIE_COLOURED, st, omax_mode=B.EPIE_OMAX_GLOBAL) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 def test_probe_sum_flag(orc):
@@ -237,7 +261,7 @@ def test_probe_sum_flag(orc):
     with engine(d, B.EPIE_COLOURED, st, flags=B.EPIE_PROBE_SUM, beta=0.25) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 @pytest.mark.parametrize("path", [B.EPIE_PATH_FUSED, B.EPIE_PATH_PLAIN])
@@ -259,7 +283,7 @@ def test_minibatch(orc, path, batch):
         eng.append(d["frames"], d["pos"])
         assert np.array_equal(eng.order(0)[0], order)
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 # --------------------------------------------------------------------------- live mode
@@ -292,7 +316,7 @@ def test_live_append_between_sweeps(orc):
             eng.append(d["frames"][n:n + c], d["pos"][n:n + c])
             n += c
             e_g += list(eng.iterate(1))
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 def test_truncate_reverts_to_prefix():
@@ -397,7 +421,7 @@ def test_append_from_device_tensor(orc):
     with engine(d, B.EPIE_COLOURED, st) as eng:
         B.epie_append_frames_device(eng.h, t.data_ptr(), d["pos"], len(d["pos"]))
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
 
 
 def test_frames_in_fft_order_flag():
@@ -467,4 +491,4 @@ def test_minibatch_256_with_dark_field(orc):
         eng.set_dark(d["dark"])
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
-        assert_parity(eng.object(), eng.probe(), e_g, O, P, e)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)

@@ -1,0 +1,110 @@
+"""Live mode with a feeder thread (paper, Sec. "Live ePIE": one thread
+appends the frames as they arrive while another keeps iterating on the
+frames present).  A feeder thread appends chunks while the main thread runs
+epie_iterate(n); each sweep covers the frames present when it started, which
+the handle reports per sweep (epie_last_sweep_frames).  Replaying those
+counts sweep by sweep - on a second handle without threads, and on the FP64
+oracle - gives the threaded run's result."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2308_10674_gb300 import _binding as B
+from paper_2308_10674_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CHUNK, N_SWEEPS, EVERY = 4, 120, 10
+
+
+def rel(a, b):
+    return float(np.linalg.norm((np.asarray(a) - b).ravel()) / np.linalg.norm(np.ravel(b)))
+
+
+def c64(a):
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
+def test_feeder_thread_appends_while_iterating(orc):
+    d = synth.small_scan(64, 4, 4, 33, seed=12)
+    n = len(d["pos"])
+    rng = np.random.default_rng(3)
+    O0 = c64(d["O_true"] * (1 + 0.05 * synth.smooth_field(d["O_true"].shape, 2.0, rng)))
+    P0 = c64(d["P_true"] * (1 + 0.05 * synth.smooth_field(d["P_true"].shape, 2.0, rng)))
+
+    def engine():
+        return B.Engine(64, d["H"], d["W"], P0, O0, capacity=n, mode=B.EPIE_COLOURED, seed=5,
+                        device=0)
+
+    errors = []
+    with engine() as eng:
+        eng.append(d["frames"][:CHUNK], d["pos"][:CHUNK])
+
+        def feeder():
+            try:
+                go.wait()
+                for k in range(1, n // CHUNK):
+                    # the next chunk arrives once the iterating thread has queued
+                    # k*EVERY sweeps (reading the index takes the handle's mutex
+                    # between two sweeps, as the append does)
+                    t0 = time.time()
+                    while eng.sweep_index < k * EVERY and time.time() - t0 < 30:
+                        time.sleep(2e-5)
+                    a = k * CHUNK
+                    eng.append(d["frames"][a:a + CHUNK], d["pos"][a:a + CHUNK])
+            except Exception as ex:  # reported by the main thread
+                errors.append(ex)
+
+        go = threading.Event()
+        th = threading.Thread(target=feeder)
+        th.start()
+        go.set()
+        e_g = eng.iterate(N_SWEEPS)
+        th.join()
+        assert not errors, errors
+        counts = eng.last_sweep_frames()
+        O_g, P_g = eng.object(), eng.probe()
+    # every sweep saw a whole number of chunks, never fewer than the sweep before
+    assert len(counts) == N_SWEEPS and counts[0] == CHUNK
+    assert np.all(counts % CHUNK == 0) and np.all(np.diff(counts) >= 0) and counts.max() <= n
+    assert len(np.unique(counts)) >= 2, counts  # at least one chunk joined mid-call
+
+    # replay on a second handle without threads: bit for bit
+    with engine() as ref:
+        have = 0
+        e_r = []
+        for c in counts:
+            if c > have:
+                ref.append(d["frames"][have:c], d["pos"][have:c])
+                have = c
+            e_r += list(ref.iterate(1))
+        assert np.array_equal(ref.object(), O_g) and np.array_equal(ref.probe(), P_g)
+        assert np.array_equal(np.array(e_r), e_g)
+
+    # replay on the oracle: the colouring of the frames present, the sweep's
+    # order, one coloured sweep each; a chain of 120 sweeps is compared within
+    # 3x the oracle's own spread under 1e-7 perturbations of its start probe
+    I_all = orc.prepare_intensity(d["frames"])
+
+    def run(start):
+        O, P = start[0].copy(), start[1].copy()
+        es = []
+        for s, c in enumerate(counts):
+            col, ncls = orc.colour_greedy(d["pos"][:c], 64)
+            order, gs = orc.order_coloured(5, s, col, ncls)
+            er, ir = orc.sweep_groups(O, P, I_all, d["pos"], order, gs)
+            es.append(er / ir)
+        return O, P, np.array(es)
+
+    O, P, e = run((O0, P0))
+    sp = [0.0, 0.0, 0.0]
+    for k in range(2):
+        Z = np.random.default_rng(100 + k).standard_normal(P0.shape)
+        O2, P2, e2 = run((O0, P0 * (1 + 1e-7 * Z)))
+        sp = [max(sp[0], rel(O2, O)), max(sp[1], rel(P2, P)),
+              max(sp[2], float(np.max(np.abs(e2 - e) / e)))]
+    assert rel(O_g, O) <= 3 * sp[0] + 1e-5, (rel(O_g, O), sp)
+    assert rel(P_g, P) <= 3 * sp[1] + 1e-5, (rel(P_g, P), sp)
+    assert np.max(np.abs(e_g - e) / e) <= 3 * sp[2] + 1e-6, sp

@@ -30,10 +30,17 @@ def start_state(d):
     return O.astype(np.complex64), P.astype(np.complex64)
 
 
-@pytest.mark.parametrize("N,ny,nx,step", [(64, 4, 5, 33), (256, 3, 4, 130)])
-def test_static_scratch_step_matches_engine(N, ny, nx, step):
+# (N, raster ny x nx, step, dark field, probe moved by the mean): 64^2 with the
+# probe sum, 128^2 with a dark field, 256^2, and 512^2 with one class of 16
+# disjoint members (the entry point's member limit at that size)
+CASES = [(64, 4, 5, 33, False, False), (128, 3, 4, 66, True, True),
+         (256, 3, 4, 130, False, True), (512, 4, 4, 520, False, True)]
+
+
+@pytest.mark.parametrize("N,ny,nx,step,dark,mean", CASES)
+def test_static_scratch_step_matches_engine(N, ny, nx, step, dark, mean):
     torch = pytest.importorskip("torch")
-    d = synth.small_scan(N, ny, nx, step, seed=N + 1)
+    d = synth.small_scan(N, ny, nx, step, seed=N + 1, dark=dark)
     O0, P0 = start_state(d)
     n = len(d["pos"])
     dev = torch.device("cuda", 0)
@@ -44,12 +51,20 @@ def test_static_scratch_step_matches_engine(N, ny, nx, step):
     fft_frames = np.ascontiguousarray(np.fft.ifftshift(d["frames"], axes=(-2, -1)))
     F_t = torch.from_numpy(fft_frames.view(np.int16)).to(dev)
     pos_t = torch.from_numpy(np.ascontiguousarray(d["pos"], np.int32)).to(dev)
+    dark_t = None
+    if dark:
+        dark_t = torch.from_numpy(
+            np.ascontiguousarray(np.fft.ifftshift(d["dark"]), np.float32)).to(dev)
     torch.cuda.synchronize(dev)
 
     eng = B.Engine(N, d["H"], d["W"], P0, O0, capacity=n, mode=B.EPIE_COLOURED, seed=5,
-                   device=0)
+                   device=0, flags=0 if mean else B.EPIE_PROBE_SUM)
     try:
+        if dark:
+            eng.set_dark(d["dark"])
         eng.append(d["frames"], d["pos"])
+        if N == 512:
+            assert eng.n_classes == 1  # all 16 members in one group
         for sweep in range(2):
             order, gs = eng.order(sweep)
             mem_t = torch.from_numpy(order.astype(np.int32)).to(dev)
@@ -59,6 +74,7 @@ def test_static_scratch_step_matches_engine(N, ny, nx, step):
                 e, s = B.epie_group_step_static(
                     N, B.EPIE_U16, O_t.data_ptr(), d["H"], d["W"], P_t.data_ptr(),
                     F_t.data_ptr(), n, pos_t.data_ptr(), mem_t.data_ptr() + 4 * a, b - a,
+                    dark_ptr=None if dark_t is None else dark_t.data_ptr(), probe_mean=mean,
                     stream=stream.cuda_stream)
                 e_sum += e
                 s_sum += s
@@ -91,3 +107,21 @@ def test_static_scratch_limits_are_rejected():
         B.epie_group_step_static(64, B.EPIE_U16, p, 128, 128, p, p, 4, pos.data_ptr(),
                                  ids.data_ptr(), 2)
     assert ex.value.code == B.EPIE_EINVAL and "outside" in str(ex.value)
+
+
+def test_static_misaligned_pointers_are_rejected():
+    """Caller-lent buffers at odd offsets are refused before any launch: the
+    step copies frame rows with bulk copies (16-byte aligned source), reads
+    the object as float2 and the probe reduction moves the probe as float4."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    buf = torch.zeros(1 << 16, dtype=torch.float32, device=dev)
+    p = buf.data_ptr()
+    ids = torch.zeros(1, dtype=torch.int32, device=dev)
+    pos = torch.zeros(2, dtype=torch.int32, device=dev)
+    for obj, prb, frm, why in ((p + 4, p, p, "object"), (p, p + 8, p, "probe"),
+                               (p, p, p + 2, "frames")):
+        with pytest.raises(B.EpieError) as ex:
+            B.epie_group_step_static(64, B.EPIE_U16, obj, 128, 128, prb, frm, 1, pos.data_ptr(),
+                                     ids.data_ptr(), 1)
+        assert ex.value.code == B.EPIE_EINVAL and why in str(ex.value)
