@@ -17,14 +17,21 @@ __device__ __forceinline__ void atomic_max_pos_double(unsigned long long *slot, 
   atomicMax(slot, static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-// block-wide max of a double (all threads return the block value)
+// |v|^2 in FP64 of the block's element of largest |v|^2 (FP32 comparisons
+// pick the element: lanes, then warps), valid in thread 0.  The FP64 square
+// is formed once per block: the FP64 pipe is narrow.
 template <int NT>
-__device__ double block_max(double v, double *sh) {
-  v = warp_max(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+__device__ double block_abs2_max(float q, float2 v, float4 *sh) {
+  v = warp_argmax_f(q, v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float4(v.x, v.y, v.x * v.x + v.y * v.y, 0.f);
   __syncthreads();
-  double m = sh[0];
-  for (int w = 1; w < NT / 32; ++w) m = fmax(m, sh[w]);
+  double m = 0.0;
+  if (threadIdx.x == 0) {
+    float4 best = sh[0];
+    for (int w = 1; w < NT / 32; ++w)
+      if (sh[w].z > best.z) best = sh[w];
+    m = static_cast<double>(best.x) * best.x + static_cast<double>(best.y) * best.y;
+  }
   __syncthreads();
   return m;
 }
@@ -73,7 +80,7 @@ __global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
     float2 *__restrict__ P, const float2 *__restrict__ part, int n_members, int K, float scale,
     unsigned long long *pmax2_next, const int32_t *gstart, int group, int mean) {
   __shared__ float4 acc_sh[PR_ROWS][32];
-  __shared__ double sh[PR_THREADS / 32];
+  __shared__ float4 sh[PR_THREADS / 32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (gstart) {  // group size from the device table
     n_members = gstart[group + 1] - gstart[group];
@@ -123,15 +130,14 @@ __global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
     }
     __syncthreads();
   }
-  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
-  d = block_max<PR_THREADS>(d, sh);
+  const double d = block_abs2_max<PR_THREADS>(best, bv, sh);
   if (threadIdx.x == 0) atomic_max_pos_double(pmax2_next, d);
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT) abs2_max_kernel(const float2 *__restrict__ a, long long n,
                                                       unsigned long long *out) {
-  __shared__ double sh[NT / 32];
+  __shared__ float4 sh[NT / 32];
   float best = -1.f;
   float2 bv = make_float2(0.f, 0.f);
   for (long long i = blockIdx.x * static_cast<long long>(NT) + threadIdx.x; i < n;
@@ -140,8 +146,7 @@ __global__ void __launch_bounds__(NT) abs2_max_kernel(const float2 *__restrict__
     const float q = p.x * p.x + p.y * p.y;
     if (q > best) { best = q; bv = p; }
   }
-  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
-  d = block_max<NT>(d, sh);
+  const double d = block_abs2_max<NT>(best, bv, sh);
   if (threadIdx.x == 0) atomic_max_pos_double(out, d);
 }
 
@@ -175,7 +180,8 @@ __global__ void __launch_bounds__(NT) error_reduce_kernel(const double *__restri
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = ss[0] > 0.0 ? se[0] / ss[0] : 0.0;
+  // 0 for an empty sweep; a non-finite sum gives a non-finite error
+  if (threadIdx.x == 0) *out = ss[0] == 0.0 ? 0.0 : se[0] / ss[0];
 }
 
 // ---------------------------------------------------------------- plain path
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(NT) error_reduce_kernel(const double *__restri
 // psi[m] = P . O_j for every member; max|O_j|^2 per member (bits)
 __global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi,
                                     unsigned long long *__restrict__ omax_bits) {
-  __shared__ double sh[8];
+  __shared__ float4 sh[8];
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
   const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
@@ -196,8 +202,7 @@ __global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi
     const float q = o.x * o.x + o.y * o.y;
     if (q > best) { best = q; bv = o; }
   }
-  double d = static_cast<double>(bv.x) * bv.x + static_cast<double>(bv.y) * bv.y;
-  d = block_max<256>(d, sh);
+  const double d = block_abs2_max<256>(best, bv, sh);
   if (threadIdx.x == 0) atomic_max_pos_double(omax_bits + m, d);
 }
 
@@ -205,7 +210,7 @@ __global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi
 // 4 elements per block, per-block error partials
 template <typename IT>
 __global__ void plain_modulus_kernel(GroupArgs a, int N, float2 *__restrict__ Psi) {
-  __shared__ double se[8], ss[8];
+  __shared__ float4 red[8];
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
   const IT *I = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * K;
@@ -234,21 +239,37 @@ __global__ void plain_modulus_kernel(GroupArgs a, int N, float2 *__restrict__ Ps
     e = fmaf(d, d, e);
     s += In;
   }
-  double de = warp_sum(static_cast<double>(e)), ds = warp_sum(static_cast<double>(s));
-  if ((threadIdx.x & 31) == 0) {
-    se[threadIdx.x >> 5] = de;
-    ss[threadIdx.x >> 5] = ds;
-  }
+  // FP32 per thread, error-free FP32 trees per warp, FP64 across warps (one thread)
+  float el = 0.f, sl = 0.f;
+  warp_two_sum(e, el);
+  warp_two_sum(s, sl);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float4(e, el, s, sl);
   __syncthreads();
   if (threadIdx.x == 0) {
     double te = 0.0, ts = 0.0;
     for (int w = 0; w < 8; ++w) {
-      te += se[w];
-      ts += ss[w];
+      te += two_sum_value(red[w].x, red[w].y);
+      ts += two_sum_value(red[w].z, red[w].w);
     }
     a.err_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = te;
     a.isum_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = ts;
   }
+}
+
+// (alpha_eff / max|P|^2, beta / max|O|^2) of a member, once per block
+// (thread 0; FP64 maxima, FP32 divisions) and handed to every thread
+// through shared memory
+__device__ float2 block_strengths(const GroupArgs &a, unsigned long long omax_bits, float alpha_eff) {
+  __shared__ float2 st;
+  if (threadIdx.x == 0) {
+    const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+    const double om = a.omax2_global ? *a.omax2_global
+                                     : __longlong_as_double(static_cast<long long>(omax_bits));
+    st = make_float2(pm > 0.0 ? alpha_eff / static_cast<float>(pm) : 0.f,
+                     om > 0.0 ? a.beta / static_cast<float>(om) : 0.f);
+  }
+  __syncthreads();
+  return st;
 }
 
 // O patch update and probe partial from psi' (= inverse cuFFT output)
@@ -257,11 +278,8 @@ __global__ void plain_update_kernel(GroupArgs a, int N, const float2 *__restrict
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
   const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
-  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
-  const double om = a.omax2_global ? *a.omax2_global
-                                   : __longlong_as_double(static_cast<long long>(omax_bits[m]));
-  const float ao = pm > 0.0 ? static_cast<float>(static_cast<double>(a.alpha) / pm) : 0.f;
-  const float bp = om > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om) : 0.f;
+  const float2 st = block_strengths(a, omax_bits[m], a.alpha);
+  const float ao = st.x, bp = st.y;
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
     const int y = i / N, x = i % N;
@@ -284,11 +302,8 @@ __global__ void mb_accumulate_kernel(GroupArgs a, int N, const float2 *__restric
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
   const int py = a.pos[2 * f], px = a.pos[2 * f + 1];
-  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
-  const double om = a.omax2_global ? *a.omax2_global
-                                   : __longlong_as_double(static_cast<long long>(omax_bits[m]));
-  const float ao = pm > 0.0 ? static_cast<float>(1.0 / pm) : 0.f;
-  const float bp = om > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om) : 0.f;
+  const float2 st = block_strengths(a, omax_bits[m], 1.0f);
+  const float ao = st.x, bp = st.y;
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.pmax2_clear) *a.pmax2_clear = 0ull;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
     const int y = i / N, x = i % N;
@@ -371,7 +386,8 @@ cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st) {
 
 namespace {
 // Measured amplitude of frames [f0, f0 + n) in FFT order: amp = sqrt(max(I -
-// dark, 0)), and the frame's sum of max(I - dark, 0) in FP64.  One block per
+// dark, 0)), and the frame's sum of max(I - dark, 0) (error-free FP32 per thread, FP64
+// across threads).  One block per
 // frame; each thread sums a fixed set of elements and the block adds the
 // thread sums in a fixed order, so the sums do not depend on scheduling.
 template <typename IT>
@@ -381,15 +397,15 @@ __global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__
                                                          double *__restrict__ isum, int f0, int K) {
   __shared__ double sh[1024];
   const size_t base = static_cast<size_t>(f0 + blockIdx.x) * K;
-  double s = 0.0;
+  float s = 0.f, cc = 0.f;  // error-free FP32 sum (the FP64 pipe is narrow)
   for (int i = threadIdx.x; i < K; i += 1024) {
     float v = ival(frames[base + i]);
     if (dark) v -= dark[i];
     v = fmaxf(v, 0.f);
-    s += static_cast<double>(v);
+    two_sum_add(s, cc, v);
     amp[base + i] = sqrtf(v);
   }
-  sh[threadIdx.x] = s;
+  sh[threadIdx.x] = two_sum_value(s, cc);
   __syncthreads();
   for (int w = 512; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -402,6 +418,8 @@ __global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__
 cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
                               double *isum, int f0, int n, int N, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  // 256^2: the step kernel's own tile layout (epie_fused_256.cu)
+  if (N == 256) return launch_amp_ingest_256(frames, itype, dark, amp, isum, f0, n, st);
   const int K = N * N;
   if (itype == EPIE_U16)
     amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp, isum,

@@ -398,6 +398,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
       : "r"(taddr)
       : "memory");
 }
+// 8 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -445,6 +454,32 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;
+}
+
+// s + c += v, error-free in FP32 (Knuth's two-sum): the pair (s, c) carries
+// the exact sum of the values added to about 2^-48 relative, without the
+// FP64 pipe (narrow on this GPU)
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float v) {
+  const float t = s + v, bp = t - s;
+  c += (s - (t - bp)) + (v - bp);
+  s = t;
+}
+
+// the value of a two-sum pair in FP64; an infinite sum stays infinite (its
+// error term is NaN then)
+__device__ __forceinline__ double two_sum_value(float hi, float lo) {
+  return isfinite(hi) ? static_cast<double>(hi) + static_cast<double>(lo) : static_cast<double>(hi);
+}
+
+// (hi, lo) <- the warp's sum of the lanes' (hi + lo), two-sum at every level
+// of the butterfly tree (lane 0's result is the one to use)
+__device__ __forceinline__ void warp_two_sum(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    two_sum_add(hi, lo, h2);
+    lo += l2;
+  }
 }
 
 // intensity element -> float

@@ -295,10 +295,14 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(slab, q));
       t4[i] = src[crank * CH + off];
     }
-    // one remote load per lane: lane q < CL fetches CTA q's patch maximum
-    double om_all = lane < CL ? *cluster.map_shared_rank(red, lane) : 0.0;
+    // one remote load per lane of warp 0: lane q < CL fetches CTA q's patch
+    // maximum (FP64 only in this warp: the FP64 pipe is narrow)
+    double om_all = 0.0;
+    if (warp == 0) {
+      om_all = lane < CL ? *cluster.map_shared_rank(red, lane) : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) om_all = fmax(om_all, __shfl_xor_sync(0xffffffffu, om_all, o));
+      for (int o = 16; o > 0; o >>= 1) om_all = fmax(om_all, __shfl_xor_sync(0xffffffffu, om_all, o));
+    }
     EPIE_PHASE(4);
     cluster.sync();  // all remote reads done before the tile is overwritten
 #pragma unroll
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
     EPIE_PHASE(5);
   } else {
     __syncthreads();  // red[0] written by thread 0
-    omax = red[0];
+    if (tid == 0) omax = red[0];
   }
 
   // ---------------------------------------------------------------- phase 2
@@ -364,6 +368,16 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
         a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(es);
         a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] =
             a.amp ? (crank == 0 ? a.amp_isum[f] : 0.0) : static_cast<double>(ss);
+        // the update strengths, once per CTA (FP64 maxima, FP32 divisions:
+        // the FP64 pipe is narrow); the error sums above are consumed, so
+        // their slots carry the strengths to every thread (the next barrier
+        // comes before phase 3 reads them)
+        const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+        const double om_used = a.omax2_global ? *a.omax2_global : omax;
+        const float pmf = static_cast<float>(pm), omf = static_cast<float>(om_used);
+        rede[0] = pm > 0.0 ? a.alpha / pmf : 0.f;
+        rede[1] = om_used > 0.0 ? a.beta / omf : 0.f;
+        rede[2] = pm > 0.0 ? 1.0f / pmf : 0.f;
       }
     }
   }
@@ -395,10 +409,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   fft_all<N, true, NT, WC, false, ColA>(slab, tw);
   EPIE_PHASE(12);
 
-  const double pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
-  const double om_used = a.omax2_global ? *a.omax2_global : omax;
-  const float ao = pm > 0.0 ? static_cast<float>(static_cast<double>(a.alpha) / pm) : 0.f;
-  const float bp = om_used > 0.0 ? static_cast<float>(static_cast<double>(a.beta) / om_used) : 0.f;
+  const float *strength = reinterpret_cast<const float *>(red + 2);
+  const float ao = strength[0], bp = strength[1];
   float2 *part = a.probe_part + static_cast<size_t>(member) * N * N + crank * WC;
   if (ok && a.accO == nullptr) {
 #pragma unroll
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   } else if (ok) {
     // mini-batch: patches of a batch may overlap; the object moves once per
     // batch by the count-normalised sum, applied by a separate kernel
-    const float inv_pm = pm > 0.0 ? static_cast<float>(1.0 / pm) : 0.f;
+    const float inv_pm = strength[2];
     const size_t obase = static_cast<size_t>(py) * orow + px + crank * WC;
     float ko[2 * EB], kp[2 * EB];  // a batch of kept object / probe values
 #pragma unroll
@@ -478,6 +490,11 @@ cudaError_t launch_fused_t(const GroupArgs &a, cudaStream_t st) {
   if (!configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(C::SMEM));
+    if (e != cudaSuccess) return e;
+    // prefer the whole unified L1 / shared-memory array as shared memory
+    // (2 resident CTAs of this size)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -16,7 +16,7 @@ from paper_2308_10674_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-CHUNK, N_SWEEPS, EVERY = 4, 120, 10
+CHUNK, N_SWEEPS, EVERY = 4, 200, 8
 
 
 def rel(a, b):
@@ -44,7 +44,6 @@ def test_feeder_thread_appends_while_iterating(orc):
 
         def feeder():
             try:
-                go.wait()
                 for k in range(1, n // CHUNK):
                     # the next chunk arrives once the iterating thread has queued
                     # k*EVERY sweeps (reading the index takes the handle's mutex
@@ -57,10 +56,11 @@ def test_feeder_thread_appends_while_iterating(orc):
             except Exception as ex:  # reported by the main thread
                 errors.append(ex)
 
-        go = threading.Event()
+        # the feeder polls the sweep index before the sweeps start, so its
+        # start-up latency does not race them
         th = threading.Thread(target=feeder)
         th.start()
-        go.set()
+        time.sleep(0.05)
         e_g = eng.iterate(N_SWEEPS)
         th.join()
         assert not errors, errors
@@ -84,25 +84,30 @@ def test_feeder_thread_appends_while_iterating(orc):
         assert np.array_equal(np.array(e_r), e_g)
 
     # replay on the oracle: the colouring of the frames present, the sweep's
-    # order, one coloured sweep each; a chain of 120 sweeps is compared within
-    # 3x the oracle's own spread under 1e-7 perturbations of its start probe
+    # order, one coloured sweep each.  A chain of 200 sweeps is compared
+    # within 3x the oracle's own spread when relative perturbations of 1e-7
+    # (the size of an FP32 rounding) enter its state after every sweep, as
+    # the engine's rounding does
     I_all = orc.prepare_intensity(d["frames"])
 
-    def run(start):
+    def run(start, noise_seed=None):
         O, P = start[0].copy(), start[1].copy()
+        rng = None if noise_seed is None else np.random.default_rng(noise_seed)
         es = []
         for s, c in enumerate(counts):
             col, ncls = orc.colour_greedy(d["pos"][:c], 64)
             order, gs = orc.order_coloured(5, s, col, ncls)
             er, ir = orc.sweep_groups(O, P, I_all, d["pos"], order, gs)
             es.append(er / ir)
+            if rng is not None:
+                O *= 1 + 1e-7 * rng.standard_normal(O.shape)
+                P *= 1 + 1e-7 * rng.standard_normal(P.shape)
         return O, P, np.array(es)
 
     O, P, e = run((O0, P0))
     sp = [0.0, 0.0, 0.0]
     for k in range(2):
-        Z = np.random.default_rng(100 + k).standard_normal(P0.shape)
-        O2, P2, e2 = run((O0, P0 * (1 + 1e-7 * Z)))
+        O2, P2, e2 = run((O0, P0), noise_seed=100 + k)
         sp = [max(sp[0], rel(O2, O)), max(sp[1], rel(P2, P)),
               max(sp[2], float(np.max(np.abs(e2 - e) / e)))]
     assert rel(O_g, O) <= 3 * sp[0] + 1e-5, (rel(O_g, O), sp)
