@@ -59,6 +59,8 @@ def parse():
                     help="at most this many frames per colour class (0: no cap)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-geometry-b", action="store_true",
+                    help="skip the geometry-B sweeps (object about 1400^2)")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--workload", default="live",
                     choices=["live", "multiscan", "adjoint", "live-schedule", "tc-gemm",
@@ -446,6 +448,12 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h}}
 
+    # ---- geometry B of the live workload (object about 1400^2, step about
+    # 9.7 px): the same frames and probe on a denser scan, hence many more and
+    # much smaller colour classes
+    if rank == 0 and args.geometry == "A" and N == 256 and not args.no_geometry_b:
+        line["geometry_b"] = geometry_b(args, stream, device)
+
     # ---- plain unfused path on the same workload (speedup at the same accuracy)
     if rank == 0 and not args.no_plain and args.path == "fused":
         pe = make_engine(B.EPIE_PATH_PLAIN)
@@ -479,6 +487,7 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": n_s / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one coloured FP64 oracle sweep over the first {n_s} "
                                           f"frames of the workload ({secs:.1f} s, 1 thread)"}
+        line["oracle_timings"] = oracle_timings(d, os.cpu_count() or 1)
         line["error_vs_oracle"] = {
             "sample_frames": n_s, "start": "paper's flat start (O = 1, phase-free aperture)",
             "rel_l2_object": rel(O_g, O_r), "rel_l2_probe": rel(P_g, P_r),
@@ -496,6 +505,47 @@ def run_ours(args):
     return 0
 
 
+def geometry_b(args, stream, device):
+    """Sweeps of the live workload in geometry B (all frames resident, no
+    ingest in the timed region): frame-updates/s, colour classes and the step
+    kernel's roofline fraction."""
+    import torch
+    from paper_2308_10674_gb300 import _binding as B, synth
+    N = 256
+    d = synth.live_scan(N=N, n=args.frames, geometry="B", seed=0, workers=args.workers)
+    n = len(d["pos"])
+    eng = B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=n, mode=B.EPIE_COLOURED, seed=5,
+                   device=device, stream=stream.cuda_stream)
+    eng.set_dark(d["dark"])
+    eng.append(d["frames"], d["pos"])
+    steps = max(3, args.steps // 2)
+    eng.iterate(2)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    eng.iterate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / steps
+    B.epie_set_kernel_timing(eng.h, True)
+    B.epie_kernel_timing(eng.h)
+    eng.iterate(2)
+    k_launches, k_ms, k_frames = B.epie_kernel_timing(eng.h)
+    classes = eng.n_classes
+    eng.close()
+    pk, _ = peaks()
+    avg = k_ms / max(k_launches, 1)
+    fpl = k_frames / max(k_launches, 1)
+    achieved = fft_flops(N) * fpl / (avg / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms, "frames": n,
+            "object": [d["H"], d["W"]], "colour_classes": classes,
+            "frames_per_launch": fpl, "avg_launch_ms": avg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak},
+            "note": "sweeps over all frames, no ingest in the timed region"}
+
+
 # --------------------------------------------------------------------------- other workloads
 
 MULTISCAN = [(128, 2000, "raster", "coloured"), (128, 4096, "jittered", "minibatch"),
@@ -508,7 +558,11 @@ def run_multiscan(args):
     """Eight independent scans of uneven size (128^2 / 256^2 / 512^2 frames,
     raster / jittered raster / spiral, FP16 intensity storage, noise-free
     model intensities) sweeping concurrently with graph-replayed sweeps;
-    mini-batch sizes picked by the autotuner."""
+    mini-batch sizes and the 128^2 tile shapes picked by the autotuner.
+    Beside the concurrent rate it times every scan's sweep alone: the longest
+    of those is the critical path that no schedule of the eight (streams or
+    one persistent launch) can beat, because each scan's groups run one
+    after the other."""
     import torch
     from paper_2308_10674_gb300 import _binding as B, autotune, synth
     torch.cuda.set_device(0)
@@ -520,14 +574,14 @@ def run_multiscan(args):
     gen_s = time.time() - t0
     for (N, n, pat, mode), d in zip(MULTISCAN, scans):
         m = B.EPIE_MINIBATCH if mode == "minibatch" else B.EPIE_COLOURED
-        batch = 64
-        if m == B.EPIE_MINIBATCH:
-            best, _ = autotune.tune(d, mode=m, intensity_dtype=B.EPIE_F16, graph=(True,))
-            batch = best["batch"]
+        best, _ = autotune.tune(d, mode=m, intensity_dtype=B.EPIE_F16, graph=(True,))
+        batch = best["batch"] if m == B.EPIE_MINIBATCH else 64
+        tile = best.get("ctas_per_frame", 0)
         chosen.append({"N": N, "frames": n, "pattern": pat, "mode": mode,
-                       "batch": batch if m == B.EPIE_MINIBATCH else None})
+                       "batch": batch if m == B.EPIE_MINIBATCH else None,
+                       "ctas_per_frame": tile})
         e = B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=n, mode=m, batch=batch, seed=5,
-                     intensity_dtype=B.EPIE_F16, flags=B.EPIE_GRAPH)
+                     intensity_dtype=B.EPIE_F16, flags=B.EPIE_GRAPH, ctas_per_frame=tile)
         e.append(d["frames"], d["pos"])
         engines.append(e)
     handles = [e.h for e in engines]
@@ -540,9 +594,11 @@ def run_multiscan(args):
         B.epie_iterate_many(handles, 1)
     conc = (time.perf_counter() - t) / args.steps
     t = time.perf_counter()
+    alone = [0.0] * len(engines)
     for _ in range(args.steps):
-        for e in engines:
+        for i, e in enumerate(engines):
             e.iterate(1)
+            alone[i] += e.last_timing()[0] / args.steps
     seq = (time.perf_counter() - t) / args.steps
     launches = sum(B.epie_launch_count(h) for h in handles)
     for e in engines:
@@ -555,6 +611,8 @@ def run_multiscan(args):
                        "frames_total": total, "generation_s": gen_s},
             "back_to_back": {"value": total / seq, "ms_per_step": seq * 1e3,
                              "concurrency_speedup": seq / conc},
+            "critical_path": {"ms_per_sweep_alone": alone, "longest_ms": max(alone),
+                              "concurrent_over_longest": conc * 1e3 / max(alone)},
             "gpu_launches_total": launches}
     print(json.dumps(line), flush=True)
     return 0
@@ -877,6 +935,44 @@ def _oracle_window(job):
     order, gs = orc.order_coloured(5, 0, col, ncls)
     orc.sweep_groups(O, P, I_all, pos, order, gs)
     return time.perf_counter() - t
+
+
+def _oracle_config0(_):
+    """The FP64 oracle on config 0 in full: 256 positions of 64^2, ten
+    sequential sweeps from the flat start (one process)."""
+    from oracle import oracle as orc
+    from paper_2308_10674_gb300 import synth
+    d = synth.config0(seed=0)
+    I_all = orc.prepare_intensity(d["frames"])
+    O, P = d["O0"].astype(np.complex128), d["P0"].astype(np.complex128)
+    t = time.perf_counter()
+    orc.run_sweeps(O, P, I_all, d["pos"], 10, d["N"], seed=0)
+    return time.perf_counter() - t
+
+
+def oracle_timings(d, cores):
+    """The FP64 oracle as it stands, on the host cores of this run: config 0
+    in full on one core, and one coloured sweep over 500 and over 2,000
+    frames of the live 256^2 workload on one core and on all cores (one
+    process per core, each on its own window of the workload)."""
+    import multiprocessing as mp
+    n = len(d["pos"])
+    out = {"cores": cores}
+    with mp.get_context("spawn").Pool(1) as pool:
+        t0 = pool.map(_oracle_config0, [0])[0]
+    out["config0_full"] = {"frame_updates": 2560, "seconds": t0, "value": 2560 / t0, "cores": 1}
+    for n_w in (500, 2000):
+        jobs = []
+        for k in range(cores):
+            a = (k * n_w) % max(n - n_w, 1)
+            jobs.append((d["frames"][a:a + n_w], d["pos"][a:a + n_w], d["dark"], d["P0"], d["H"],
+                         d["W"], d["N"]))
+        t1 = _oracle_window(jobs[0])
+        with mp.get_context("spawn").Pool(cores) as pool:
+            times = pool.map(_oracle_window, jobs)
+        out[f"live_{n_w}"] = {"one_core": n_w / t1, "all_cores": sum(n_w / t for t in times),
+                              "seconds_one_core": t1, "max_seconds_all_cores": max(times)}
+    return out
 
 
 def run_oracle_cores(args):

@@ -151,11 +151,16 @@ typedef struct {
   int32_t class_cap;       /* EPIE_COLOURED: at most this many frames per colour
                               class (first-fit skips full classes); 0 = no cap  */
   int32_t gemm_precision;  /* EPIE_PATH_GEMM: EPIE_GEMM_*                        */
+  int32_t ctas_per_frame;  /* EPIE_PATH_FUSED, the step kernel's tile shape: CTAs
+                              (one cluster) per frame; 0 = the default (1, 2, 8,
+                              16 for N = 64, 128, 256, 512); N = 128 also builds
+                              1 and 4 (see the autotuner)                       */
 } epie_config;
 
 /* Fills *cfg with defaults: N 256, object 1024^2, capacity 1024, EPIE_U16,
  * EPIE_COLOURED, batch 64, EPIE_OMAX_PATCH, EPIE_PATH_FUSED, alpha = beta = 1,
- * seed 0, device 0, own stream, no flags, no class cap, EPIE_GEMM_BF16X3. */
+ * seed 0, device 0, own stream, no flags, no class cap, EPIE_GEMM_BF16X3,
+ * the default tile shape. */
 EPIE_API void epie_config_default(epie_config *cfg);
 
 /* Creates a handle and allocates every device buffer the configuration needs:

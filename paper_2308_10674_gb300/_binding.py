@@ -34,7 +34,8 @@ class epie_config(C.Structure):
                 ("batch", C.c_int32), ("omax_mode", C.c_int32), ("path", C.c_int32),
                 ("alpha", C.c_float), ("beta", C.c_float), ("seed", C.c_uint64),
                 ("device", C.c_int32), ("stream", C.c_void_p), ("flags", C.c_uint32),
-                ("class_cap", C.c_int32), ("gemm_precision", C.c_int32)]
+                ("class_cap", C.c_int32), ("gemm_precision", C.c_int32),
+                ("ctas_per_frame", C.c_int32)]
 
 
 class epie_amp_grad_args(C.Structure):
@@ -379,7 +380,8 @@ class Engine:
     def __init__(self, N, obj_h, obj_w, probe0, object0=None, capacity=1024,
                  intensity_dtype=EPIE_U16, mode=EPIE_COLOURED, batch=64,
                  omax_mode=EPIE_OMAX_PATCH, path=EPIE_PATH_FUSED, alpha=1.0, beta=1.0, seed=0,
-                 device=0, stream=None, flags=0, class_cap=0, gemm_precision=EPIE_GEMM_BF16X3):
+                 device=0, stream=None, flags=0, class_cap=0, gemm_precision=EPIE_GEMM_BF16X3,
+                 ctas_per_frame=0):
         cfg = epie_config_default()
         cfg.N, cfg.obj_h, cfg.obj_w, cfg.capacity = N, obj_h, obj_w, capacity
         cfg.intensity_dtype, cfg.mode, cfg.batch = intensity_dtype, mode, batch
@@ -387,6 +389,7 @@ class Engine:
         cfg.seed, cfg.device, cfg.stream, cfg.flags = seed, device, stream, flags
         cfg.class_cap = class_cap
         cfg.gemm_precision = gemm_precision
+        cfg.ctas_per_frame = ctas_per_frame
         self.cfg = cfg
         self.h = epie_init(cfg, probe0, object0)
 

@@ -349,7 +349,7 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, bool o_early
       a.inject_skip_copy = 1;
       a.wait_ns = h->inject_wait_ns;
     }
-    CK(epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st));
+    CK(epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st, h->cfg.ctas_per_frame));
     *kernels += 1;
   } else if (h->cfg.path == EPIE_PATH_GEMM) {
     std::string why;
@@ -376,7 +376,12 @@ int run_group(epie_ctx *h, const int32_t *members_d, int n_members, bool o_early
     h->kev_used += 2;
   }
   if (mb) {
-    CK(epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st));
+    // apply over the batch's patches while they cover less than the object
+    if (static_cast<long long>(n_members) * h->K < h->HW)
+      CK(epie::launch_mb_apply_local(h->O, h->accO, h->cnt, h->cfg.obj_w, h->pos_d, members_d,
+                                     n_members, nullptr, 0, N, h->cfg.alpha, h->st));
+    else
+      CK(epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st));
     *kernels += 1;
   }
   const bool mean = h->cfg.mode == EPIE_MINIBATCH ||
@@ -432,7 +437,7 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
     h->graph = nullptr;
     {  // configure the kernel (shared-memory size, cluster shape) outside the capture
       GroupArgs z{};
-      CK(epie::launch_fused(h->cfg.N, h->cfg.intensity_dtype, z, h->st));
+      CK(epie::launch_fused(h->cfg.N, h->cfg.intensity_dtype, z, h->st, h->cfg.ctas_per_frame));
     }
     const int N = h->cfg.N;
     const bool mb = h->cfg.mode == EPIE_MINIBATCH;
@@ -471,9 +476,16 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
         ce = epie::launch_object_max(h->O, h->HW, h->omax_glob, h->omax_tmp, h->st);
         a.omax2_global = h->omax_glob;
       }
-      if (ce == cudaSuccess) ce = epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st);
-      if (ce == cudaSuccess && mb)
-        ce = epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st);
+      if (ce == cudaSuccess)
+        ce = epie::launch_fused(N, h->cfg.intensity_dtype, a, h->st, h->cfg.ctas_per_frame);
+      if (ce == cudaSuccess && mb) {
+        if (static_cast<long long>(maxg) * h->K < h->HW)
+          ce = epie::launch_mb_apply_local(h->O, h->accO, h->cnt, h->cfg.obj_w, h->pos_d,
+                                           h->order_d, maxg, h->gstart_d, g, N, h->cfg.alpha,
+                                           h->st);
+        else
+          ce = epie::launch_mb_apply(h->O, h->accO, h->cnt, h->HW, h->cfg.alpha, h->st);
+      }
       if (ce == cudaSuccess)
         ce = epie::launch_probe_reduce_table(h->P, h->probe_part, h->gstart_d, g, mean, N,
                                              h->pmax2 + (p ^ 1), h->st);
@@ -641,6 +653,8 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH | EPIE_FRAMES_FFT_ORDER))
     why = "unknown flags";
   else if (c.class_cap < 0) why = "class_cap must be >= 0";
+  else if (c.path == EPIE_PATH_FUSED && epie::fused_ctas_per_frame(c.N, c.ctas_per_frame) == 0)
+    why = "ctas_per_frame: tile shape not built for this N (0 = default; 1, 2, 4 at N = 128)";
   if (!why.empty()) {
     g_init_error = "epie_init: " + why;
     return EPIE_EINVAL;
@@ -661,7 +675,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   h->HW = static_cast<long long>(c.obj_h) * c.obj_w;
   // partial error slots per frame: one per CTA of the fused kernel, one per
   // block of the plain path's modulus kernel; every slot is written each sweep
-  h->err_stride = c.path == EPIE_PATH_FUSED ? epie::fused_ctas_per_frame(c.N)
+  h->err_stride = c.path == EPIE_PATH_FUSED ? epie::fused_ctas_per_frame(c.N, c.ctas_per_frame)
                                             : epie::plain_err_stride(c.N);  // plain and GEMM
   h->cell_rows = (c.obj_h + c.N - 1) / c.N;
   h->cell_cols = (c.obj_w + c.N - 1) / c.N;

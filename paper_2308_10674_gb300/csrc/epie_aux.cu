@@ -337,6 +337,39 @@ __global__ void mb_apply_kernel(float2 *__restrict__ O, float2 *__restrict__ acc
   }
 }
 
+// The same over the batch's footprint only: every pixel of every member's
+// N x N patch.  A pixel covered by several patches is visited several times;
+// the visitor that takes its count (atomic exchange with 0) applies and
+// clears it, the others find 0.  Member ids come from the group table
+// (members of group `group` when gstart is set).
+__global__ void mb_apply_local_kernel(float2 *__restrict__ O, float2 *__restrict__ accO,
+                                      int *__restrict__ cnt, int W, const int32_t *__restrict__ pos,
+                                      const int32_t *__restrict__ members, int n_members,
+                                      const int32_t *__restrict__ gstart, int group, int N,
+                                      float alpha) {
+  if (gstart) {
+    members += gstart[group];
+    n_members = gstart[group + 1] - gstart[group];
+  }
+  const int m = blockIdx.y;
+  if (m >= n_members) return;
+  const int f = members[m];
+  const int py = pos[2 * f], px = pos[2 * f + 1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N; i += gridDim.x * blockDim.x) {
+    const size_t oi = static_cast<size_t>(py + i / N) * W + px + i % N;
+    const int c = atomicExch(cnt + oi, 0);
+    if (c > 0) {
+      const float2 u = accO[oi];
+      const float s = alpha / static_cast<float>(c);
+      float2 o = O[oi];
+      o.x = fmaf(s, u.x, o.x);
+      o.y = fmaf(s, u.y, o.y);
+      O[oi] = o;
+      accO[oi] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
 __global__ void fill_kernel(float2 *__restrict__ p, long long n, float2 v) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -543,6 +576,16 @@ cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
 cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
                             cudaStream_t st) {
   mb_apply_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(O, accO, cnt, n, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mb_apply_local(float2 *O, float2 *accO, int *cnt, int W, const int32_t *pos,
+                                  const int32_t *members, int n_members, const int32_t *gstart,
+                                  int group, int N, float alpha, cudaStream_t st) {
+  if (n_members <= 0) return cudaSuccess;
+  dim3 grid((N * N + 1023) / 1024, n_members);
+  mb_apply_local_kernel<<<grid, 256, 0, st>>>(O, accO, cnt, W, pos, members, n_members, gstart,
+                                              group, N, alpha);
   return cudaGetLastError();
 }
 

@@ -112,7 +112,7 @@ constexpr int fused_min_blocks() {
 #ifdef EPIE_FUSED_MIN_BLOCKS
   return EPIE_FUSED_MIN_BLOCKS;
 #else
-  return CL == 1 ? 2 : (1024 / NT > 1 ? 1024 / NT : 1);
+  return CL == 1 && NT <= 256 ? 2 : (1024 / NT > 1 ? 1024 / NT : 1);
 #endif
 }
 

@@ -71,10 +71,12 @@ struct GroupArgs {
 // error-flag bits written by kernels
 enum : int { FLAG_TMA_TIMEOUT = 1, FLAG_TC_TIMEOUT = 2 };
 
-// fused kernel: one group, dispatch on N and intensity type
-cudaError_t launch_fused(int N, int itype, const GroupArgs &a, cudaStream_t st);
-// CTAs per frame used by the fused kernel for this N (error slots per frame)
-int fused_ctas_per_frame(int N);
+// fused kernel: one group, dispatch on N, intensity type and tile shape (cl:
+// CTAs per frame, 0 = the default for N)
+cudaError_t launch_fused(int N, int itype, const GroupArgs &a, cudaStream_t st, int cl = 0);
+// CTAs per frame of the fused kernel for this N and tile shape (error slots
+// per frame); 0 when that shape is not built
+int fused_ctas_per_frame(int N, int cl = 0);
 // dynamic shared memory of the fused kernel (for diagnostics)
 size_t fused_smem_bytes(int N, int itype);
 
@@ -130,6 +132,12 @@ cudaError_t launch_mb_accumulate(const GroupArgs &a, int N, const float2 *psi1,
                                  const double *omax2, float2 *accO, int *cnt, cudaStream_t st);
 cudaError_t launch_mb_apply(float2 *O, float2 *accO, int *cnt, long long n, float alpha,
                             cudaStream_t st);
+// the same over the batch's patches only (cheaper while batch x N^2 is below
+// the object size); members from `members` or, with gstart, from the group
+// table; grid sized for n_members
+cudaError_t launch_mb_apply_local(float2 *O, float2 *accO, int *cnt, int W, const int32_t *pos,
+                                  const int32_t *members, int n_members, const int32_t *gstart,
+                                  int group, int N, float alpha, cudaStream_t st);
 
 // failure injection for the timeout tests: the next `count` tcgen05 GEMM
 // calls skip the first operand copy on CTA 0 and bound their waits by wait_ns

@@ -50,6 +50,7 @@ int main(void) {{
 #define F(m) printf(" %zu", offsetof(epie_config, m));
   F(N) F(obj_h) F(obj_w) F(capacity) F(intensity_dtype) F(mode) F(batch) F(omax_mode) F(path)
   F(alpha) F(beta) F(seed) F(device) F(stream) F(flags) F(class_cap) F(gemm_precision)
+  F(ctas_per_frame)
   return 0;
 }}
 """)

@@ -492,3 +492,30 @@ def test_minibatch_256_with_dark_field(orc):
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+# --------------------------------------------------------------------------- mini-batch at the multi-scan batch sizes
+
+@pytest.mark.parametrize("N,n,batch", [(128, 1024, 1024), (128, 512, 64), (256, 192, 64)])
+def test_minibatch_at_multiscan_batch_sizes(orc, N, n, batch):
+    """Mini-batch sweeps at the batch sizes the multi-scan workload and its
+    autotuner use (64 to 1024 members; 1024 overlapping patches accumulate
+    into one batch's object update), jittered-raster scans of the live
+    model, against the oracle's mini-batch sweep (reading R7)."""
+    d = synth.scan(N, n, "jittered", seed=60 + N + batch, photons=1e8)
+    st = textured_start(d)
+    I_all = orc.prepare_intensity(d["frames"])
+    order = orc.order_sequential(5, 0, n)
+
+    def run(s0):
+        O, P = s0[0].copy(), s0[1].copy()
+        er, ir = orc.sweep_minibatch(O, P, I_all, d["pos"], order, batch)
+        return O, P, np.array([er / ir])
+
+    (O, P, e), sp = spread(run, st, samples=1)
+    assert max(sp[:2]) <= WELL_CONDITIONED, sp
+    with engine(d, B.EPIE_MINIBATCH, st, batch=batch) as eng:
+        eng.append(d["frames"], d["pos"])
+        assert np.array_equal(eng.order(0)[0], order)
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
