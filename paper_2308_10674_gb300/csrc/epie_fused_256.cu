@@ -83,6 +83,9 @@ static __device__ long long g_phase_clocks[4096][16];
 namespace {
 
 constexpr int S_N = 256, S_CL = 8, S_NT = 512, S_NW = 16;
+// clusters (frames) one wave of this kernel holds on a GB300 (2 CTAs per SM;
+// measured: the first wave of a 65-member group started 35 clusters)
+constexpr int S_WAVE = 35;
 static_assert(EPIE_CTAS_256 == S_CL, "the 256^2 kernel runs 8-CTA clusters");
 constexpr int CP = 33;                       // column-tile pitch (complex)
 constexpr int RP = 257;                      // row-tile pitch (complex)
@@ -170,11 +173,13 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
   EPIE_PHASE(0);
   const int member = blockIdx.x / S_CL;
   const int32_t *members = a.members;
+  int n_members = a.n_members;
   if (a.gstart) {
     // device group table: a whole cluster past the group's size exits here,
     // before any barrier or copy
     const int g0 = a.gstart[a.group];
-    if (member >= a.gstart[a.group + 1] - g0) return;
+    n_members = a.gstart[a.group + 1] - g0;
+    if (member >= n_members) return;
     members += g0;
   }
   const int c = static_cast<int>(cluster_rank());
@@ -245,6 +250,18 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
       tmem_st16(tm + 16 * h, keep);
     }
   };
+  // A group larger than one wave of clusters runs a second wave: warm L2 with
+  // the object rows of the frame that will take this cluster's place there
+  // (a hint only; a prefetch of lines still being written is harmless).
+  if (member + S_WAVE < n_members && tid < S_N) {
+    const int f2 = members[member + S_WAVE];
+    const float2 *row = a.O + static_cast<size_t>(a.pos[2 * f2] + tid) * a.W + a.pos[2 * f2 + 1] + 32 * c;
+    // the 16-byte-aligned interior of the 256-byte row segment (never past it)
+    const uintptr_t b0 = (reinterpret_cast<uintptr_t>(row) + 15) & ~static_cast<uintptr_t>(15);
+    const uintptr_t b1 = (reinterpret_cast<uintptr_t>(row + 32)) & ~static_cast<uintptr_t>(15);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"(static_cast<uint32_t>(b1 - b0))
+                 : "memory");
+  }
   // The object patch is read before the dependency wait when o_early says it
   // is final; the probe, max|P|^2 and the partial buffers are written by the
   // preceding kernels and are read after it.
@@ -257,19 +274,28 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
   // early: the update strengths are formed after the first transpose
   double pm = 0.0;
   if (tid == 0) pm = __longlong_as_double(static_cast<long long>(*a.pmax2));
+  // the probe: with the object values parked, v takes all 16 probe values in
+  // one round trip; the exit wave multiplies the parked object values back in
+  tmem_wait_st();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = __ldg(Pb + r * 16 * S_N);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    float2 pv[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) pv[i] = __ldg(Pb + (8 * h + i) * 16 * S_N);
     float keep[16];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      keep[2 * i] = pv[i].x;
-      keep[2 * i + 1] = pv[i].y;
-      v[8 * h + i] = cmul(pv[i], v[8 * h + i]);
+      keep[2 * i] = v[8 * h + i].x;
+      keep[2 * i + 1] = v[8 * h + i].y;
     }
     tmem_st16(tm + 32 + 16 * h, keep);
+  }
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float ko[8];
+    tmem_ld8(tm + 8 * h, ko);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[4 * h + i] = cmul(v[4 * h + i], make_float2(ko[2 * i], ko[2 * i + 1]));
   }
   EPIE_PHASE(1);
   // column stage A
