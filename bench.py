@@ -91,12 +91,12 @@ def fft_flops(N):
 
 
 def source_hash():
-    """Hash of the fused 256^2 kernel's code: its sources with // comments,
+    """Hash of the 256^2 step kernel's code: its sources with // comments,
     trailing blanks and empty lines removed, so that a comment edit keeps a
     traffic record taken on the same code."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2308_10674_gb300", "csrc")
-    for f in ("epie_fft.cuh", "epie_fused.cuh", "epie_fused_256.cu"):
+    for f in ("epie_fft.cuh", "epie_fused_256.cu"):
         with open(os.path.join(d, f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()

@@ -102,6 +102,7 @@ struct epie_ctx {
   float2 *probe_part = nullptr;
   int part_cap = 0;             // members the probe_part buffer holds
   double *err_part = nullptr, *isum_part = nullptr;
+  double *err_blocks = nullptr;         // 2 * ERR_BLOCKS block sums of the sweep error
   int err_stride = 1;
   unsigned long long *pmax2 = nullptr;  // [2] double bits
   int pslot = 0;                        // slot holding max|P|^2 of the current probe
@@ -494,7 +495,7 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
     if (ce == cudaSuccess && p == 1) ce = epie::launch_copy_u64(h->pmax2 + 1, h->pmax2, h->st);
     if (ce == cudaSuccess)
       ce = epie::launch_error_reduce(h->err_part, h->isum_part, n, h->err_stride, h->err_sweep,
-                                     h->st);
+                                     h->err_blocks, h->st);
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(h->st, &graph);
     if (ce != cudaSuccess) {
@@ -512,7 +513,7 @@ int run_sweep_graph(epie_ctx *h, int slot, const std::vector<int32_t> &order,
   const bool mb = h->cfg.mode == EPIE_MINIBATCH;
   *kernels += static_cast<int64_t>(ng) * (2 + (mb ? 1 : 0) +
                                           (h->cfg.omax_mode == EPIE_OMAX_GLOBAL ? 2 : 0)) +
-              1 + (ng % 2);
+              2 + (ng % 2);
   return EPIE_OK;
 }
 
@@ -541,8 +542,8 @@ int run_sweep(epie_ctx *h, int slot, int64_t *kernels) {
     if (rc) return rc;
   }
   CK(epie::launch_error_reduce(h->err_part, h->isum_part, n, h->err_stride, h->err_out + slot,
-                               h->st));
-  *kernels += 1;
+                               h->err_blocks, h->st));
+  *kernels += 2;
   if (h->ktime && h->kev_used > 0) {
     CK(cudaEventSynchronize(h->kev[h->kev_used - 1]));
     for (int i = 0; i < h->kev_used; i += 2) {
@@ -602,7 +603,7 @@ int epie_destroy(epie_t h) {
       if (h->ev_order[b]) cudaEventDestroy(h->ev_order[b]);
     }
     void *dev[] = {h->gstart_d, h->err_sweep, h->O, h->P, h->twiddle, h->frames, h->pos_d, h->order_d, h->dark_d,
-                   h->probe_part, h->err_part, h->isum_part, h->pmax2, h->omax_glob,
+                   h->probe_part, h->err_part, h->err_blocks, h->isum_part, h->pmax2, h->omax_glob,
                    h->omax_tmp, h->err_out, h->flag_d, h->O_keep, h->P_keep, h->psi,
                    h->omax_m, h->accO, h->cnt, h->stage_d, h->amp, h->amp_isum};
     for (void *p : dev)
@@ -717,6 +718,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
     IK(cudaMalloc(&h->amp_isum, sizeof(double) * static_cast<size_t>(cap)));
   }
   IK(cudaMalloc(&h->err_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
+  IK(cudaMalloc(&h->err_blocks, sizeof(double) * 2 * epie::ERR_BLOCKS));
   IK(cudaMalloc(&h->isum_part, sizeof(double) * h->err_stride * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->pmax2, sizeof(unsigned long long) * 2));
   IK(cudaMalloc(&h->omax_glob, sizeof(double)));

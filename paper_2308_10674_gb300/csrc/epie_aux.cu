@@ -96,18 +96,18 @@ __global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
   for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
     const int i = base + 2 * tx;  // K is a multiple of 64
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int m = ty;
-    for (; m + 3 * PR_ROWS < n_members; m += 4 * PR_ROWS) {
-      const float4 a0 = ld(m, i), a1 = ld(m + PR_ROWS, i), a2 = ld(m + 2 * PR_ROWS, i),
-                   a3 = ld(m + 3 * PR_ROWS, i);
-      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
-      acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
-      acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
-      acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
-    }
-    for (; m < n_members; m += PR_ROWS) {
-      const float4 a0 = ld(m, i);
-      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+    // up to 8 member loads in flight per thread (a class of 64 is one round)
+    for (int m0 = ty; m0 < n_members; m0 += 8 * PR_ROWS) {
+      float4 ld8[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int m = m0 + k * PR_ROWS;
+        ld8[k] = m < n_members ? ld(m, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc.x += ld8[k].x; acc.y += ld8[k].y; acc.z += ld8[k].z; acc.w += ld8[k].w;
+      }
     }
     acc_sh[ty][tx] = acc;
     __syncthreads();
@@ -181,6 +181,55 @@ __global__ void __launch_bounds__(NT) error_reduce_kernel(const double *__restri
     __syncthreads();
   }
   // 0 for an empty sweep; a non-finite sum gives a non-finite error
+  if (threadIdx.x == 0) *out = ss[0] == 0.0 ? 0.0 : se[0] / ss[0];
+}
+
+// Stage 1 of the sweep error: block b sums frames [b per, (b + 1) per) (thread
+// t takes frames b per + t, + 256, ..., all slots of each in order), then a
+// fixed tree over the threads; writes (sum e, sum s) of its range.
+__global__ void __launch_bounds__(256) error_block_kernel(const double *__restrict__ e,
+                                                          const double *__restrict__ s,
+                                                          int n_frames, int stride, int per,
+                                                          double *__restrict__ blocks) {
+  __shared__ double se[256], ss[256];
+  const int f0 = blockIdx.x * per, f1 = min(n_frames, f0 + per);
+  double a = 0.0, b = 0.0;
+  for (int f = f0 + threadIdx.x; f < f1; f += 256)
+    for (int c = 0; c < stride; ++c) {
+      a += e[static_cast<size_t>(f) * stride + c];
+      b += s[static_cast<size_t>(f) * stride + c];
+    }
+  se[threadIdx.x] = a;
+  ss[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    blocks[2 * blockIdx.x] = se[0];
+    blocks[2 * blockIdx.x + 1] = ss[0];
+  }
+}
+
+// Stage 2: E = sum e / sum s over the ERR_BLOCKS block sums (fixed tree); 0
+// for an empty sweep, non-finite when a sum is
+__global__ void __launch_bounds__(ERR_BLOCKS) error_final_kernel(const double *__restrict__ blocks,
+                                                                 double *out) {
+  __shared__ double se[ERR_BLOCKS], ss[ERR_BLOCKS];
+  se[threadIdx.x] = blocks[2 * threadIdx.x];
+  ss[threadIdx.x] = blocks[2 * threadIdx.x + 1];
+  __syncthreads();
+  for (int h = ERR_BLOCKS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) *out = ss[0] == 0.0 ? 0.0 : se[0] / ss[0];
 }
 
@@ -531,8 +580,16 @@ cudaError_t launch_object_max(const float2 *O, long long n, double *out, unsigne
 }
 
 cudaError_t launch_error_reduce(const double *err_part, const double *isum_part, int n_frames,
-                                int stride, double *out, cudaStream_t st) {
-  error_reduce_kernel<1024><<<1, 1024, 0, st>>>(err_part, isum_part, n_frames, stride, out);
+                                int stride, double *out, double *blocks, cudaStream_t st) {
+  // two fixed-order stages: ERR_BLOCKS blocks over contiguous frame ranges,
+  // then one block over their sums (FP64 adds spread over many SMs: the FP64
+  // pipe of a single SM made one block the bottleneck)
+  const int per = (n_frames + ERR_BLOCKS - 1) / ERR_BLOCKS;
+  error_block_kernel<<<ERR_BLOCKS, 256, 0, st>>>(err_part, isum_part, n_frames, stride, per,
+                                                 blocks);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  error_final_kernel<<<1, ERR_BLOCKS, 0, st>>>(blocks, out);
   return cudaGetLastError();
 }
 

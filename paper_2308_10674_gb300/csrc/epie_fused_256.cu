@@ -568,41 +568,49 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
 // frequency ky = (p >> 4) + 16 (p & 15)) holds, as float4 chunk
 // (k1 * 4 + m) * 32 + yl, the values at kx = k1 + 16 (4 m + i), i = 0..3.
 // amp = sqrt(max(I - dark, 0)); isum = sum of max(I - dark, 0), two-sum in
-// FP32 per thread and a fixed-order FP64 sum over the block.
+// FP32 per thread and a fixed-order FP64 sum over the block.  One block per
+// frame walks the 8 tiles: the tile's 32 frequency rows are read row by row
+// (coalesced) into shared memory, then written chunk by chunk (coalesced).
+constexpr int AI_NT = 256, AI_PITCH = S_N + 1;  // odd pitch: conflict-free chunk reads
 template <typename IT>
-__global__ void __launch_bounds__(512) amp_ingest256_kernel(const IT *__restrict__ frames,
-                                                            const float *__restrict__ dark,
-                                                            float *__restrict__ amp,
-                                                            double *__restrict__ isum, int f0) {
-  __shared__ double sh[512];
+__global__ void __launch_bounds__(AI_NT) amp_ingest256_kernel(const IT *__restrict__ frames,
+                                                              const float *__restrict__ dark,
+                                                              float *__restrict__ amp,
+                                                              double *__restrict__ isum, int f0) {
+  __shared__ float rows[32 * AI_PITCH];
+  __shared__ double sh[AI_NT];
   const size_t fb = static_cast<size_t>(f0 + blockIdx.x) * S_N * S_N;
   const IT *fr = frames + fb;
   float4 *out = reinterpret_cast<float4 *>(amp + fb);
+  const int t = threadIdx.x;
   float s = 0.f, cc = 0.f;
-  for (int ci = threadIdx.x; ci < S_N * S_N / 4; ci += 512) {
-    const int q = ci >> 11, cj = ci & 2047, yl = cj & 31, k1m = cj >> 5;
-    const int k1 = k1m >> 2, m = k1m & 3;
-    const int ky = freq_of_pos(32 * q + yl);
-    float4 o;
-    float *op = &o.x;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int kx = k1 + 16 * (4 * m + i);
-      float I = ival(fr[ky * S_N + kx]);
-      if (dark) I -= __ldg(dark + ky * S_N + kx);
-      I = fmaxf(I, 0.f);
+  for (int q = 0; q < S_CL; ++q) {
+#pragma unroll 4
+    for (int yl = 0; yl < 32; ++yl) {
+      const int ky = freq_of_pos(32 * q + yl);
+      float I = ival(fr[ky * S_N + t]);
+      if (dark) I -= __ldg(dark + ky * S_N + t);
+      I = fmaxf(I, 0.f);  // also maps NaN to 0
       two_sum_add(s, cc, I);
-      op[i] = sqrtf(I);
+      rows[yl * AI_PITCH + t] = sqrtf(I);
     }
-    out[ci] = o;
-  }
-  sh[threadIdx.x] = two_sum_value(s, cc);
-  __syncthreads();
-  for (int h = 256; h > 0; h >>= 1) {
-    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2048 / AI_NT; ++u) {
+      const int cj = t + AI_NT * u, yl = cj & 31, k1m = cj >> 5;
+      const int k1 = k1m >> 2, m = k1m & 3;
+      const float *r = rows + yl * AI_PITCH + k1 + 64 * m;
+      out[q * 2048 + cj] = make_float4(r[0], r[16], r[32], r[48]);
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) isum[f0 + blockIdx.x] = sh[0];
+  sh[t] = two_sum_value(s, cc);
+  __syncthreads();
+  for (int h = AI_NT / 2; h > 0; h >>= 1) {
+    if (t < h) sh[t] += sh[t + h];
+    __syncthreads();
+  }
+  if (t == 0) isum[f0 + blockIdx.x] = sh[0];
 }
 
 bool g_tw_ready[64] = {};
@@ -677,14 +685,14 @@ cudaError_t launch_amp_ingest_256(const void *frames, int itype, const float *da
                                   double *isum, int f0, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (itype == 0)
-    amp_ingest256_kernel<<<n, 512, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp,
-                                           isum, f0);
+    amp_ingest256_kernel<<<n, AI_NT, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp,
+                                             isum, f0);
   else if (itype == 1)
-    amp_ingest256_kernel<<<n, 512, 0, st>>>(static_cast<const __half *>(frames), dark, amp, isum,
-                                           f0);
+    amp_ingest256_kernel<<<n, AI_NT, 0, st>>>(static_cast<const __half *>(frames), dark, amp,
+                                             isum, f0);
   else
-    amp_ingest256_kernel<<<n, 512, 0, st>>>(static_cast<const float *>(frames), dark, amp, isum,
-                                           f0);
+    amp_ingest256_kernel<<<n, AI_NT, 0, st>>>(static_cast<const float *>(frames), dark, amp,
+                                             isum, f0);
   return cudaGetLastError();
 }
 

@@ -98,8 +98,11 @@ cudaError_t launch_probe_max(const float2 *P, int K, unsigned long long *pmax2, 
 cudaError_t launch_object_max(const float2 *O, long long n, double *out, unsigned long long *tmp,
                               cudaStream_t st);
 // sweep error: E = sum e / sum s over frames [0, n_frames), fixed order
+// blocks: device scratch of 2 * ERR_BLOCKS doubles (per handle: concurrent
+// sweeps of several handles must not share it)
+constexpr int ERR_BLOCKS = 128;
 cudaError_t launch_error_reduce(const double *err_part, const double *isum_part, int n_frames,
-                                int stride, double *out, cudaStream_t st);
+                                int stride, double *out, double *blocks, cudaStream_t st);
 // live ingest: raw DC-centred frames -> device set in FFT order (ifftshift)
 cudaError_t launch_ingest(const void *raw, void *dst, int n, int N, int esize, cudaStream_t st);
 // out[i] = (1/k) sum_q src[q][i] (q in order) for n complex values; src is a

@@ -15,14 +15,14 @@ import bench  # noqa: E402
 def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2308_10674_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("epie_fft.cuh", "epie_fused.cuh", "epie_fused_256.cu"):
+    for f in ("epie_fft.cuh", "epie_fused_256.cu"):
         shutil.copy(os.path.join(ROOT, "paper_2308_10674_gb300", "csrc", f), csrc / f)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.source_hash()
-    p = csrc / "epie_fused.cuh"
+    p = csrc / "epie_fused_256.cu"
     p.write_text(p.read_text() + "\n// a new comment line\n\n")
     assert bench.source_hash() == h0
-    p.write_text(p.read_text().replace("constexpr int EB", "constexpr  int EB", 1))
+    p.write_text(p.read_text().replace("constexpr int CP", "constexpr  int CP", 1))
     assert bench.source_hash() != h0
 
 
