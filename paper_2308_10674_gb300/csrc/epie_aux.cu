@@ -96,18 +96,18 @@ __global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
   for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
     const int i = base + 2 * tx;  // K is a multiple of 64
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    // up to 8 member loads in flight per thread (a class of 64 is one round)
-    for (int m0 = ty; m0 < n_members; m0 += 8 * PR_ROWS) {
-      float4 ld8[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int m = m0 + k * PR_ROWS;
-        ld8[k] = m < n_members ? ld(m, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        acc.x += ld8[k].x; acc.y += ld8[k].y; acc.z += ld8[k].z; acc.w += ld8[k].w;
-      }
+    int m = ty;
+    for (; m + 3 * PR_ROWS < n_members; m += 4 * PR_ROWS) {
+      const float4 a0 = ld(m, i), a1 = ld(m + PR_ROWS, i), a2 = ld(m + 2 * PR_ROWS, i),
+                   a3 = ld(m + 3 * PR_ROWS, i);
+      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+      acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
+      acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
+      acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
+    }
+    for (; m < n_members; m += PR_ROWS) {
+      const float4 a0 = ld(m, i);
+      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
     }
     acc_sh[ty][tx] = acc;
     __syncthreads();
