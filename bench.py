@@ -454,6 +454,30 @@ def run_ours(args):
     if rank == 0 and args.geometry == "A" and N == 256 and not args.no_geometry_b:
         line["geometry_b"] = geometry_b(args, stream, device)
 
+    # ---- the step kernel staging the raw uint16 rows (EPIE_RAW_INTENSITY) instead
+    # of the amplitudes derived at append: sweeps over the same frames
+    if rank == 0 and args.path == "fused" and not args.no_plain:
+        re_ = B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=n, mode=B.EPIE_COLOURED,
+                       seed=5, device=device, stream=stream.cuda_stream,
+                       flags=B.EPIE_RAW_INTENSITY)
+        re_.set_dark(d["dark"])
+        re_.append(frames, pos)
+        re_.iterate(1)
+        torch.cuda.synchronize(device)
+        ksteps = max(2, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        re_.iterate(ksteps)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        rms = e0.elapsed_time(e1) / ksteps
+        re_.close()
+        line["raw_intensity_staging"] = {
+            "value": n / (rms / 1e3), "unit": UNIT, "ms_per_sweep": rms,
+            "hbm_bytes_per_frame": N * N * frames.itemsize,
+            "note": "sweeps only (no ingest); the step kernel copies the uint16 rows by TMA and "
+                    "converts them itself (EPIE_RAW_INTENSITY)"}
+
     # ---- plain unfused path on the same workload (speedup at the same accuracy)
     if rank == 0 and not args.no_plain and args.path == "fused":
         pe = make_engine(B.EPIE_PATH_PLAIN)

@@ -127,6 +127,12 @@ typedef struct epie_ctx *epie_t;
                                 frequency at [0,0]) and are stored as given;
                                 without it they are DC-centred (the detector's
                                 layout) and re-laid out on the device         */
+#define EPIE_RAW_INTENSITY 16u /* fused path: the step kernel copies the stored
+                                intensity rows (uint16 / FP16 / FP32) by TMA
+                                and forms sqrt(max(I - dark, 0)) itself,
+                                instead of reading amplitudes derived at append
+                                (half the bytes per frame for uint16 and FP16,
+                                no amplitude buffer of capacity x N^2 floats) */
 #define EPIE_GRAPH 4u        /* fused path: capture a sweep's launches in a CUDA
                                 graph once and replay it each sweep (the group
                                 table is uploaded per sweep; recaptured when the

@@ -23,6 +23,7 @@ EPIE_PATH_FUSED, EPIE_PATH_PLAIN, EPIE_PATH_GEMM = 0, 1, 2
 EPIE_GEMM_BF16, EPIE_GEMM_TF32, EPIE_GEMM_BF16X3, EPIE_GEMM_FP32EMU = 0, 1, 2, 3
 EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3, EPIE_GEMM_TC_TF32, EPIE_GEMM_TC_TF32X3 = 4, 5, 6, 7
 EPIE_CHECKED, EPIE_PROBE_SUM, EPIE_GRAPH, EPIE_FRAMES_FFT_ORDER = 1, 2, 4, 8
+EPIE_RAW_INTENSITY = 16
 
 STATUS = {0: "EPIE_OK", -1: "EPIE_EINVAL", -2: "EPIE_ERANGE", -3: "EPIE_ECAPACITY",
           -4: "EPIE_ECUDA", -5: "EPIE_ETIMEOUT", -6: "EPIE_ENUMERIC", -7: "EPIE_ESTATE"}

@@ -651,7 +651,8 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   else if (c.gemm_precision < EPIE_GEMM_BF16 || c.gemm_precision > EPIE_GEMM_TC_TF32X3)
     why = "bad gemm_precision";
   else if (!std::isfinite(c.alpha) || !std::isfinite(c.beta)) why = "alpha and beta must be finite";
-  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH | EPIE_FRAMES_FFT_ORDER))
+  else if (c.flags & ~(EPIE_CHECKED | EPIE_PROBE_SUM | EPIE_GRAPH | EPIE_FRAMES_FFT_ORDER |
+                       EPIE_RAW_INTENSITY))
     why = "unknown flags";
   else if (c.class_cap < 0) why = "class_cap must be >= 0";
   else if (c.path == EPIE_PATH_FUSED && epie::fused_ctas_per_frame(c.N, c.ctas_per_frame) == 0)
@@ -713,7 +714,7 @@ int epie_init(epie_t *out, const epie_config *cfg, const float *probe0, const fl
   IK(cudaMalloc(&h->pos_d, sizeof(int32_t) * 2 * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->order_d, sizeof(int32_t) * static_cast<size_t>(cap)));
   IK(cudaMalloc(&h->dark_d, sizeof(float) * h->K));
-  if (c.path == EPIE_PATH_FUSED) {
+  if (c.path == EPIE_PATH_FUSED && !(c.flags & EPIE_RAW_INTENSITY)) {
     IK(cudaMalloc(&h->amp, sizeof(float) * h->K * static_cast<size_t>(cap)));
     IK(cudaMalloc(&h->amp_isum, sizeof(double) * static_cast<size_t>(cap)));
   }

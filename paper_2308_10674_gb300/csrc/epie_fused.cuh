@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   bool ok = mbar_wait_bounded(bar, 0, wait_ns);
   if (!ok) atomicOr(a.err_flag, FLAG_TMA_TIMEOUT);
   ok = __all_sync(0xffffffffu, ok);  // warp-uniform: phase 3 reads TMEM warp-collectively
-  float isum_t = 0.f;  // sum I of this thread's tile elements
+  float isum_t = 0.f, isum_c = 0.f;  // two-sum of I over this thread's tile elements
   if (!a.amp) {
     // intensity tile -> float max(I - dark, 0), in place: the raw tile sits
     // at the top of the float tile, so every raw value is read (and the dark
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
 #pragma unroll
     for (int i = 0; i < EI; ++i) {
       const float I = fmaxf(iv[i], 0.f);
-      isum_t += I;
+      two_sum_add(isum_t, isum_c, I);
       itile[tid + i * NT] = sqrtf(I);
     }
     // the first row pass's barrier orders these writes before the modulus
@@ -352,22 +352,30 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
   fft_roundtrip_rows<N, NT, HR, RowB>(slab, tw, mod);
   EPIE_PHASE(7);
   {
-    // FP32 within the CTA (lanes, then warps), FP64 across CTAs and frames
+    // FP32 over a thread's elements, error-free (two-sum) FP32 trees over the
+    // warp, FP64 across warps, CTAs and frames
     float *rede = reinterpret_cast<float *>(red + 2);
-    const float e = warp_sum_f(mod.e), s = warp_sum_f(isum_t);
-    if (lane == 0) {
-      rede[2 * warp] = e;
-      rede[2 * warp + 1] = s;
-    }
+    float eh = mod.e, el = 0.f, sh = isum_t, sl = isum_c;
+    warp_two_sum(eh, el);
+    warp_two_sum(sh, sl);
+    if (lane == 0) reinterpret_cast<float4 *>(rede)[warp] = make_float4(eh, el, sh, sl);
     __syncthreads();
     if (warp == 0) {
-      float es = lane < NW ? rede[2 * lane] : 0.f, ss = lane < NW ? rede[2 * lane + 1] : 0.f;
-      es = warp_sum_f(es);
-      ss = warp_sum_f(ss);
+      double es = 0.0, ss = 0.0;
+      if (lane < NW) {
+        const float4 t4 = reinterpret_cast<const float4 *>(rede)[lane];
+        es = two_sum_value(t4.x, t4.y);
+        ss = two_sum_value(t4.z, t4.w);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        es += __shfl_xor_sync(0xffffffffu, es, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      }
       if (lane == 0) {
-        a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = static_cast<double>(es);
+        a.err_part[static_cast<size_t>(f) * a.err_stride + crank] = es;
         a.isum_part[static_cast<size_t>(f) * a.err_stride + crank] =
-            a.amp ? (crank == 0 ? a.amp_isum[f] : 0.0) : static_cast<double>(ss);
+            a.amp ? (crank == 0 ? a.amp_isum[f] : 0.0) : ss;
         // the update strengths, once per CTA (FP64 maxima, FP32 divisions:
         // the FP64 pipe is narrow); the error sums above are consumed, so
         // their slots carry the strengths to every thread (the next barrier

@@ -519,3 +519,25 @@ def test_minibatch_at_multiscan_batch_sizes(orc, N, n, batch):
         assert np.array_equal(eng.order(0)[0], order)
         e_g = eng.iterate(1)
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+@pytest.mark.parametrize("N,ny,nx,step", [(64, 4, 5, 33), (256, 2, 3, 130)])
+def test_raw_intensity_staging(orc, N, ny, nx, step):
+    """EPIE_RAW_INTENSITY: the step kernel copies the stored uint16 rows and
+    forms sqrt(max(I - dark, 0)) itself.  Against the oracle (sharp, with a
+    dark field), and object and probe bit-identical to the derived-amplitude
+    path (the same FP32 operations on the same values; only the intensity
+    sum of the error metric is added in another order)."""
+    d = synth.small_scan(N, ny, nx, step, seed=N + 7, dark=True, photons=1e7)
+    st = textured_start(d)
+    O, P, e = sharp(orc, d, B.EPIE_COLOURED, st)
+    outs = []
+    for flags in (0, B.EPIE_RAW_INTENSITY):
+        with engine(d, B.EPIE_COLOURED, st, flags=flags) as eng:
+            eng.set_dark(d["dark"])
+            eng.append(d["frames"], d["pos"])
+            e_g = eng.iterate(1)
+            assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+            outs.append((eng.object(), eng.probe(), e_g))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert abs(outs[0][2][0] - outs[1][2][0]) <= 1e-12 * outs[0][2][0]
