@@ -51,8 +51,11 @@
  *   - Host buffers belong to the caller; a call has finished reading or
  *     writing them when it returns.  The engine owns all device memory.
  *   - Calls on one handle are serialised by a mutex; epie_iterate releases it
- *     between sweeps, so frames appended by another thread during
- *     epie_iterate join at the next sweep boundary.
+ *     between sweeps and, while another call waits for it, hands it over
+ *     before the next sweep, so frames appended by another thread during
+ *     epie_iterate join at the next sweep boundary (Sec. "Live ePIE").  An
+ *     append waits on the device for the sweeps already queued, so it never
+ *     overwrites frames they still read (after epie_truncate_frames).
  *   - Every call returns EPIE_OK (0) or a negative status; epie_error() then
  *     holds a message.  After EPIE_ECUDA or EPIE_ETIMEOUT the handle only
  *     accepts epie_error and epie_destroy (EPIE_ESTATE otherwise).
