@@ -67,16 +67,26 @@ __device__ __forceinline__ float2 tw16(float2 a) {
   }
 }
 
+// Packed complex add and subtract for the butterflies: one paired-FP32
+// instruction (sm_100 family) in place of two scalar ones.  Each lane rounds
+// exactly like the scalar operation, and b * (-1) + a is a - b with one
+// rounding, so the results are bit-identical to cadd / csub.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 // ------------------------------------------------------------------ small DFTs (natural order, in place)
 
 template <bool INV>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  const float2 t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2);
+  const float2 t2 = padd(a1, a3), d = psub(a1, a3);
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  // t1 -+ i d: the swapped components stay scalar
+  a1 = INV ? make_float2(t1.x - d.y, t1.y + d.x) : make_float2(t1.x + d.y, t1.y - d.x);
+  a3 = INV ? make_float2(t1.x + d.y, t1.y - d.x) : make_float2(t1.x - d.y, t1.y + d.x);
 }
 
 template <bool INV>
@@ -85,10 +95,10 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
   dft4<INV>(v[1], v[3], v[5], v[7]);  // odd part  O[k] at v[2k+1]
   const float2 o0 = v[1], o1 = tw16<2, INV>(v[3]), o2 = tw16<4, INV>(v[5]), o3 = tw16<6, INV>(v[7]);
   const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+  v[0] = padd(e0, o0); v[4] = psub(e0, o0);
+  v[1] = padd(e1, o1); v[5] = psub(e1, o1);
+  v[2] = padd(e2, o2); v[6] = psub(e2, o2);
+  v[3] = padd(e3, o3); v[7] = psub(e3, o3);
 }
 
 // 16 = 4 x 4: n = 4m + t, k = k1 + 4 k2;

@@ -438,12 +438,12 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       for (int i = 0; i < EB; ++i) {
         const int idx = tid + (i0 + i) * NT, y = idx / WC, xl = idx % WC;
         const float2 psi1 = slab[ColA::at(xl, y)];
-        const float2 d = csub(psi1, cmul(pv[i], ov[i]));
+        const float2 d = psub(psi1, cmul(pv[i], ov[i]));
         const float2 uo = cmulc(pv[i], d);  // conj(P) Delta
         const float2 up = cmulc(ov[i], d);  // conj(O_old) Delta
-        EPIE_ST_O(Obase + y * orow + xl,
-                  make_float2(fmaf(ao, uo.x, ov[i].x), fmaf(ao, uo.y, ov[i].y)));
-        part[y * N + xl] = cscale(up, bp);
+        // paired-FP32 scalings (each lane rounds as the scalar fmaf / multiply)
+        EPIE_ST_O(Obase + y * orow + xl, __ffma2_rn(make_float2(ao, ao), uo, ov[i]));
+        part[y * N + xl] = __fmul2_rn(up, make_float2(bp, bp));
       }
     }
   } else if (ok) {

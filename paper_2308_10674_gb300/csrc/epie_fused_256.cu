@@ -504,6 +504,9 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
   float2 *part = a.probe_part + static_cast<size_t>(member) * S_N * S_N + w * S_N + 32 * c + lane;
   if (ok) {
     if constexpr (!MB) {
+      // the per-element scalings as paired-FP32 operations (each lane rounds
+      // as the scalar fmaf / multiply would)
+      const float2 ao2 = make_float2(ao, ao), bp2 = make_float2(bp, bp);
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         float ko[8], kp[8];  // four elements at a time keep the registers below the limit
@@ -515,12 +518,11 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
           const int r = 4 * h + i;
           const float2 o = make_float2(ko[2 * i], ko[2 * i + 1]);
           const float2 p = make_float2(kp[2 * i], kp[2 * i + 1]);
-          const float2 d = csub(v[r], cmul(p, o));
+          const float2 d = psub(v[r], cmul(p, o));
           const float2 uo = cmulc(p, d);  // conj(P) Delta
           const float2 up = cmulc(o, d);  // conj(O_old) Delta
-          st_l2hint(Ob + static_cast<size_t>(16 * r) * orow,
-                    make_float2(fmaf(ao, uo.x, o.x), fmaf(ao, uo.y, o.y)), opol);
-          part[16 * r * S_N] = cscale(up, bp);
+          st_l2hint(Ob + static_cast<size_t>(16 * r) * orow, __ffma2_rn(ao2, uo, o), opol);
+          part[16 * r * S_N] = __fmul2_rn(up, bp2);
         }
       }
     } else {
