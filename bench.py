@@ -96,7 +96,7 @@ def source_hash():
     traffic record taken on the same code."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2308_10674_gb300", "csrc")
-    for f in ("epie_fft.cuh", "epie_fused_256.cu"):
+    for f in ("epie_fft.cuh", "epie_cluster.cuh", "epie_fused_256.cu"):
         with open(os.path.join(d, f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()

@@ -500,8 +500,10 @@ __global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__
 cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
                               double *isum, int f0, int n, int N, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  // 256^2: the step kernel's own tile layout (epie_fused_256.cu)
+  // 256^2 and 512^2: the step kernels' own tile layouts (epie_fused_256.cu,
+  // epie_fused_512.cu)
   if (N == 256) return launch_amp_ingest_256(frames, itype, dark, amp, isum, f0, n, st);
+  if (N == 512) return launch_amp_ingest_512(frames, itype, dark, amp, isum, f0, n, st);
   const int K = N * N;
   if (itype == EPIE_U16)
     amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp, isum,

@@ -128,6 +128,65 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
   t = v[11]; v[11] = v[14]; v[14] = t;
 }
 
+// cos / sin of 2 pi e / 32 (quarter-wave symmetry from the values at
+// e = 0..8: cos(pi/16), cos(pi/8), cos(3 pi/16), ...)
+__host__ __device__ constexpr float cos32(int e) {
+  constexpr float Q[9] = {1.f,
+                          0.980785280403230449126f,
+                          0.923879532511286756128f,
+                          0.831469612302545237079f,
+                          0.707106781186547524401f,
+                          0.555570233019602224743f,
+                          0.382683432365089771728f,
+                          0.195090322016128267848f,
+                          0.f};
+  const int m = e & 31;
+  return m <= 8 ? Q[m] : m <= 16 ? -Q[16 - m] : m <= 24 ? -Q[m - 16] : Q[32 - m];
+}
+__host__ __device__ constexpr float sin32(int e) { return cos32(e - 8); }
+
+// a * W32^E with W32 = exp(-+ 2 pi i / 32) (forward: minus)
+template <int E, bool INV>
+__device__ __forceinline__ float2 tw32(float2 a) {
+  constexpr int e = E & 31;
+  if constexpr ((e & 1) == 0) {
+    return tw16<e / 2, INV>(a);
+  } else {
+    constexpr float c = cos32(e);
+    constexpr float s = INV ? sin32(e) : -sin32(e);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+template <bool INV, int K>
+__device__ __forceinline__ void dft32_combine(const float2 (&e)[16], const float2 (&o)[16],
+                                              float2 (&lo)[16], float2 (&hi)[16]) {
+  if constexpr (K < 16) {
+    const float2 t = tw32<K, INV>(o[K]);
+    lo[K] = padd(e[K], t);
+    hi[K] = psub(e[K], t);
+    dft32_combine<INV, K + 1>(e, o, lo, hi);
+  }
+}
+
+// 32-point DFT of x[0..31] = (lo[0..15], hi[0..15]) in natural order, in
+// place (decimation in time: two 16-point DFTs of the even and the odd
+// samples, X[k] = E[k] + W32^k O[k], X[k + 16] = E[k] - W32^k O[k])
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&lo)[16], float2 (&hi)[16]) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    e[m] = lo[2 * m];
+    o[m] = lo[2 * m + 1];
+    e[m + 8] = hi[2 * m];
+    o[m + 8] = hi[2 * m + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+  dft32_combine<INV, 0>(e, o, lo, hi);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
   if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
@@ -439,6 +498,12 @@ __device__ __forceinline__ void grid_dependents_launch() {
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+// the same as a butterfly: every lane ends with the (identical) sum
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 __device__ __forceinline__ float warp_sum_f(float v) {

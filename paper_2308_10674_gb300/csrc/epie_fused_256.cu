@@ -50,6 +50,7 @@
 
 #include <cmath>
 
+#include "epie_cluster.cuh"
 #include "epie_fft.cuh"
 #include "epie_internal.h"
 
@@ -118,33 +119,6 @@ __constant__ float2 c_tw256[S_N];  // exp(-2 pi i m / 256)
 // (p >> 4) + 16 (p & 15)
 __device__ __forceinline__ int freq_of_pos(int p) { return (p >> 4) + 16 * (p & 15); }
 
-// ---------------------------------------------------------------- cluster PTX
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// arrive: release of this thread's prior memory operations; wait: acquire
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// shared::cluster address of `saddr` (a shared::cta address) in CTA `rank`
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y)
-               : "memory");
-}
-__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-
 template <bool INV>
 __device__ __forceinline__ float2 tw256(int m) {
   float2 w = c_tw256[m];
@@ -152,11 +126,6 @@ __device__ __forceinline__ float2 tw256(int m) {
   return w;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 template <typename IT, bool MB>
 __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
@@ -473,8 +442,8 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
       es = two_sum_value(t.x, t.y);
       ss = two_sum_value(t.z, t.w);
     }
-    es = warp_sum_d(es);
-    ss = warp_sum_d(ss);
+    es = warp_sum_all(es);
+    ss = warp_sum_all(ss);
     if (lane == 0) {
       a.err_part[static_cast<size_t>(f) * a.err_stride + c] = es;
       a.isum_part[static_cast<size_t>(f) * a.err_stride + c] =

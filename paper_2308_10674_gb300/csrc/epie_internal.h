@@ -120,6 +120,9 @@ cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, 
 // the same at N = 256, in the tile layout of the 256^2 step kernel
 cudaError_t launch_amp_ingest_256(const void *frames, int itype, const float *dark, float *amp,
                                   double *isum, int f0, int n, cudaStream_t st);
+// the same at N = 512, in the tile layout of the 512^2 step kernel
+cudaError_t launch_amp_ingest_512(const void *frames, int itype, const float *dark, float *amp,
+                                  double *isum, int f0, int n, cudaStream_t st);
 
 // plain unfused path pieces
 cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,

@@ -15,7 +15,7 @@ import bench  # noqa: E402
 def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2308_10674_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("epie_fft.cuh", "epie_fused_256.cu"):
+    for f in ("epie_fft.cuh", "epie_cluster.cuh", "epie_fused_256.cu"):
         shutil.copy(os.path.join(ROOT, "paper_2308_10674_gb300", "csrc", f), csrc / f)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.source_hash()

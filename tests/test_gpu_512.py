@@ -1,0 +1,92 @@
+"""The 512^2 step kernel (16-CTA clusters, a radix-32 and a radix-16 stage per
+axis) against the FP64 oracle through the C ABI, in every branch it has:
+derived amplitudes and raw rows of each intensity type with a dark field,
+the mini-batch instantiation, a group larger than one wave of clusters,
+graph replay from the device group table, and the global object maximum
+(paper, Sec. "ePIE Implementation"; readings R4, R5, R7 of the design notes).
+Sharp parity: one sweep from a textured start."""
+import numpy as np
+import pytest
+
+from paper_2308_10674_gb300 import _binding as B
+from paper_2308_10674_gb300 import synth
+from test_gpu_parity import (WELL_CONDITIONED, assert_parity, engine, oracle_run, sharp, spread,
+                             textured_start)
+
+pytestmark = pytest.mark.gpu
+N = 512
+
+
+@pytest.mark.parametrize("dtype,code", [(np.uint16, B.EPIE_U16), (np.float16, B.EPIE_F16),
+                                        (np.float32, B.EPIE_F32)])
+@pytest.mark.parametrize("raw", [False, True])
+def test_types_dark_and_raw_rows(orc, dtype, code, raw):
+    """Overlapping 1 x 3 raster (two classes) with a dark field; the raw path
+    converts the staged rows in the kernel, the other copies the amplitudes
+    derived at append: both against the oracle."""
+    d = synth.small_scan(N, 1, 3, 300, seed=21, dark=True, photons=1e7, dtype=dtype)
+    st = textured_start(d)
+    O, P, e = sharp(orc, d, B.EPIE_COLOURED, st)
+    with engine(d, B.EPIE_COLOURED, st, intensity_dtype=code,
+                flags=B.EPIE_RAW_INTENSITY if raw else 0) as eng:
+        eng.set_dark(d["dark"])
+        eng.append(d["frames"], d["pos"])
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+def test_group_larger_than_a_wave(orc):
+    """A 4 x 4 raster with a step of N + 2: 16 disjoint patches, one class of
+    16 clusters (more than one wave of 16-CTA clusters: the second-wave
+    prefetch and the later clusters)."""
+    d = synth.small_scan(N, 4, 4, N + 2, seed=22, jitter=0, margin=2)
+    st = textured_start(d)
+    O, P, e = oracle_run(orc, d, B.EPIE_COLOURED, 1, st)
+    with engine(d, B.EPIE_COLOURED, st) as eng:
+        eng.append(d["frames"], d["pos"])
+        assert eng.n_classes == 1
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+@pytest.mark.parametrize("batch", [2, 4])
+def test_minibatch(orc, batch):
+    d = synth.small_scan(N, 2, 3, 200, seed=23)
+    st = textured_start(d)
+    I_all = orc.prepare_intensity(d["frames"])
+    order = orc.order_sequential(5, 0, len(d["pos"]))
+
+    def run(s0):
+        O, P = s0[0].copy(), s0[1].copy()
+        er, ir = orc.sweep_minibatch(O, P, I_all, d["pos"], order, batch)
+        return O, P, np.array([er / ir])
+
+    (O, P, e), sp = spread(run, st)
+    assert max(sp[:2]) <= WELL_CONDITIONED, sp
+    with engine(d, B.EPIE_MINIBATCH, st, batch=batch) as eng:
+        eng.append(d["frames"], d["pos"])
+        assert np.array_equal(eng.order(0)[0], order)
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+def test_graph_replay_and_global_object_max(orc):
+    """Two sweeps replayed from a CUDA graph (groups read from the device
+    table, surplus clusters exit at once), with max|O|^2 over the object."""
+    d = synth.small_scan(N, 2, 3, 260, seed=512)
+    st = textured_start(d)
+    O, P, e = sharp(orc, d, B.EPIE_COLOURED, st, n_sweeps=2, omax_global=True)
+    with engine(d, B.EPIE_COLOURED, st, flags=B.EPIE_GRAPH, omax_mode=B.EPIE_OMAX_GLOBAL) as eng:
+        eng.append(d["frames"], d["pos"])
+        e_g = eng.iterate(2)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
+
+
+def test_sequential(orc):
+    d = synth.small_scan(N, 2, 2, 200, seed=25)
+    st = textured_start(d)
+    O, P, e = sharp(orc, d, B.EPIE_SEQUENTIAL, st)
+    with engine(d, B.EPIE_SEQUENTIAL, st) as eng:
+        eng.append(d["frames"], d["pos"])
+        e_g = eng.iterate(1)
+        assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
