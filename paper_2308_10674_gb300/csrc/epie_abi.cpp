@@ -811,7 +811,7 @@ int epie_set_dark(epie_t h, const float *dark) {
   h->has_dark = dark != nullptr;
   if (h->amp && h->n_frames > 0) {  // the frames' amplitudes follow the dark field
     CK(epie::launch_amp_ingest(h->frames, h->cfg.intensity_dtype, h->has_dark ? h->dark_d : nullptr,
-                               h->amp, h->amp_isum, 0, h->n_frames, h->cfg.N, h->st));
+                               h->amp, h->amp_isum, 0, h->n_frames, h->cfg.N, h->cfg.ctas_per_frame, h->st));
     h->launches_total += 1;
   }
   CK(cudaStreamSynchronize(h->st));
@@ -880,7 +880,7 @@ static int append_impl(epie_t h, const void *frames, const int32_t *pos, int32_t
   if (h->amp) {
     CK(epie::launch_amp_ingest(h->frames, h->cfg.intensity_dtype,
                                h->has_dark ? h->dark_d : nullptr, h->amp, h->amp_isum,
-                               h->n_frames, n, N, h->up));
+                               h->n_frames, n, N, h->cfg.ctas_per_frame, h->up));
     h->launches_total += 1;
   }
   CK(cudaMemcpyAsync(h->pos_d + 2 * static_cast<size_t>(h->n_frames), pos,

@@ -498,10 +498,12 @@ __global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__
 }  // namespace
 
 cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
-                              double *isum, int f0, int n, int N, cudaStream_t st) {
+                              double *isum, int f0, int n, int N, int cl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  // 256^2 and 512^2: the step kernels' own tile layouts (epie_fused_256.cu,
-  // epie_fused_512.cu)
+  // the 1-CTA 128^2, the 256^2 and the 512^2 step kernels read their own tile
+  // layouts (epie_fused_128.cu, epie_fused_256.cu, epie_fused_512.cu)
+  if (N == 128 && fused_ctas_per_frame(128, cl) == 1)
+    return launch_amp_ingest_128(frames, itype, dark, amp, isum, f0, n, st);
   if (N == 256) return launch_amp_ingest_256(frames, itype, dark, amp, isum, f0, n, st);
   if (N == 512) return launch_amp_ingest_512(frames, itype, dark, amp, isum, f0, n, st);
   const int K = N * N;

@@ -13,7 +13,7 @@
 #define EPIE_CTAS_64 1
 #endif
 #ifndef EPIE_CTAS_128
-#define EPIE_CTAS_128 2
+#define EPIE_CTAS_128 1
 #endif
 #ifndef EPIE_CTAS_256
 #define EPIE_CTAS_256 8
@@ -113,10 +113,16 @@ cudaError_t launch_average(const float2 *const *src, int k, float2 *out, long lo
 cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st);
 // dark field: DC-centred float -> FFT order
 cudaError_t launch_dark_ingest(const float *raw, float *dst, int N, cudaStream_t st);
-// amp[f] = sqrt(max(I_f - dark, 0)) (FFT order, fp32) and isum[f] = sum of
-// max(I_f - dark, 0) (FP64) for frames [f0, f0 + n) of the frame set
+// amp[f] = sqrt(max(I_f - dark, 0)) (fp32) and isum[f] = sum of
+// max(I_f - dark, 0) (FP64) for frames [f0, f0 + n) of the frame set, in the
+// layout the step kernel of tile shape cl (CTAs per frame, 0 = the default)
+// reads: FFT order, or the tile layouts of the 1-CTA 128^2, the 256^2 and the
+// 512^2 kernels
 cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, float *amp,
-                              double *isum, int f0, int n, int N, cudaStream_t st);
+                              double *isum, int f0, int n, int N, int cl, cudaStream_t st);
+// the same at N = 128 in the tile layout of the 1-CTA 128^2 step kernel
+cudaError_t launch_amp_ingest_128(const void *frames, int itype, const float *dark, float *amp,
+                                  double *isum, int f0, int n, cudaStream_t st);
 // the same at N = 256, in the tile layout of the 256^2 step kernel
 cudaError_t launch_amp_ingest_256(const void *frames, int itype, const float *dark, float *amp,
                                   double *isum, int f0, int n, cudaStream_t st);
