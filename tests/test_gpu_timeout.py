@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 WAIT_NS = 1_000_000  # 1 ms
 
 
-@pytest.mark.parametrize("N,ny,nx,step", [(64, 3, 3, 33), (256, 2, 3, 130)])
+@pytest.mark.parametrize("N,ny,nx,step", [(64, 3, 3, 33), (128, 3, 3, 65), (256, 2, 3, 130),
+                                           (512, 2, 2, 260)])
 def test_step_kernel_wait_expiry_is_reported(N, ny, nx, step):
     d = synth.small_scan(N, ny, nx, step, seed=31)
 
