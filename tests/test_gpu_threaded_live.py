@@ -17,6 +17,12 @@ from paper_2308_10674_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 CHUNK, N_SWEEPS, EVERY = 4, 160, 8
+# relative size of the perturbation that enters the oracle's state after
+# every sweep in the spread estimate: the rounding of one FP32 2-D transform
+# of K = N^2 points, about u log2(K) with u = 2^-24 (7e-7 at 64^2); a
+# perturbation of one FP32 ulp (1e-7) underestimates the engine's per-sweep
+# rounding by that factor of log2(K)
+SWEEP_ROUNDING = 1e-6
 
 
 def rel(a, b):
@@ -89,9 +95,9 @@ def test_feeder_thread_appends_while_iterating(orc):
 
     # replay on the oracle: the colouring of the frames present, the sweep's
     # order, one coloured sweep each.  A chain of 160 sweeps is compared
-    # within 3x the oracle's own spread when relative perturbations of 1e-7
-    # (the size of an FP32 rounding) enter its state after every sweep, as
-    # the engine's rounding does
+    # within 3x the oracle's own spread when relative perturbations of the
+    # size of the engine's per-sweep rounding (SWEEP_ROUNDING) enter its state
+    # after every sweep
     I_all = orc.prepare_intensity(d["frames"])
 
     def run(start, noise_seed=None):
@@ -104,8 +110,8 @@ def test_feeder_thread_appends_while_iterating(orc):
             er, ir = orc.sweep_groups(O, P, I_all, d["pos"], order, gs)
             es.append(er / ir)
             if rng is not None:
-                O *= 1 + 1e-7 * rng.standard_normal(O.shape)
-                P *= 1 + 1e-7 * rng.standard_normal(P.shape)
+                O *= 1 + SWEEP_ROUNDING * rng.standard_normal(O.shape)
+                P *= 1 + SWEEP_ROUNDING * rng.standard_normal(P.shape)
         return O, P, np.array(es)
 
     O, P, e = run((O0, P0))
