@@ -28,6 +28,21 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// Packed complex add and subtract for the butterflies: one paired-FP32
+// instruction (sm_100 family) in place of two scalar ones.  Each lane rounds
+// exactly like the scalar operation, and b * (-1) + a is a - b with one
+// rounding, so the results are bit-identical to cadd / csub.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// a * (c + i s) as a.x (c, s) + a.y (-s, c): two paired-FP32 instructions
+// with a component of a broadcast to both lanes, in place of two multiplies
+// and two fused multiply-adds
+__device__ __forceinline__ float2 cmul_const(float2 a, float c, float s) {
+  return __ffma2_rn(make_float2(a.y, a.y), make_float2(-s, c), __fmul2_rn(make_float2(a.x, a.x), make_float2(c, s)));
+}
+
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {
@@ -63,17 +78,8 @@ __device__ __forceinline__ float2 tw16(float2 a) {
   } else {
     constexpr float c = cos16(e);
     constexpr float s = INV ? sin16(e) : -sin16(e);
-    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    return cmul_const(a, c, s);
   }
-}
-
-// Packed complex add and subtract for the butterflies: one paired-FP32
-// instruction (sm_100 family) in place of two scalar ones.  Each lane rounds
-// exactly like the scalar operation, and b * (-1) + a is a - b with one
-// rounding, so the results are bit-identical to cadd / csub.
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
 // ------------------------------------------------------------------ small DFTs (natural order, in place)
@@ -154,7 +160,7 @@ __device__ __forceinline__ float2 tw32(float2 a) {
   } else {
     constexpr float c = cos32(e);
     constexpr float s = INV ? sin32(e) : -sin32(e);
-    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    return cmul_const(a, c, s);
   }
 }
 
