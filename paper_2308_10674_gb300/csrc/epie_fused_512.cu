@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(S_NT, 1) epie_fused512_kernel(GroupArgs a) {
           const float ia = rsqrtf(a2);
           amp = a2 * ia;
           const float rr = sq[i] * ia * invK;
-          z = make_float2(z.x * rr, z.y * rr);
+          z = __fmul2_rn(z, make_float2(rr, rr));  // both components, one instruction
         } else {
           amp = 0.f;
           z = make_float2(sq[i] * invK, 0.f);
