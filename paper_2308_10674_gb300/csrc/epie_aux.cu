@@ -2,6 +2,7 @@
 // the per-group probe reduction with its FP64 max|P|^2, FP64 maxima and the
 // sweep-error reduction, and the pieces of the plain unfused path
 // (gather / modulus / update) that runs the same step with cuFFT in between.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "../../include/epie.h"
@@ -236,8 +237,11 @@ __global__ void __launch_bounds__(ERR_BLOCKS) error_final_kernel(const double *_
 // ---------------------------------------------------------------- plain path
 
 // psi[m] = P . O_j for every member; max|O_j|^2 per member (bits)
+// psi = P . O_j per member, or (hi set) psi split into bf16 hi = bf16(psi)
+// and lo = bf16(psi - hi) for the tensor-core DFT (lo may be null)
 __global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi,
-                                    unsigned long long *__restrict__ omax_bits) {
+                                    unsigned long long *__restrict__ omax_bits,
+                                    __nv_bfloat162 *__restrict__ hi, __nv_bfloat162 *__restrict__ lo) {
   __shared__ float4 sh[8];
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
@@ -247,7 +251,15 @@ __global__ void plain_gather_kernel(GroupArgs a, int N, float2 *__restrict__ psi
   for (int i = blockIdx.x * 256 + threadIdx.x; i < K; i += gridDim.x * 256) {
     const int y = i / N, x = i % N;
     const float2 o = a.O[static_cast<size_t>(py + y) * a.W + px + x];
-    psi[static_cast<size_t>(m) * K + i] = cmul(a.P[i], o);
+    const float2 v = cmul(a.P[i], o);
+    const size_t t = static_cast<size_t>(m) * K + i;
+    if (hi) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+      hi[t] = h;
+      if (lo) lo[t] = __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
+    } else {
+      psi[t] = v;
+    }
     const float q = o.x * o.x + o.y * o.y;
     if (q > best) { best = q; bv = o; }
   }
@@ -600,12 +612,13 @@ cudaError_t launch_error_reduce(const double *err_part, const double *isum_part,
 int plain_err_stride(int N) { return N * N / 1024; }
 
 cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,
-                                cudaStream_t st) {
+                                cudaStream_t st, void *hi, void *lo) {
   auto *bits = reinterpret_cast<unsigned long long *>(omax2);
   cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * a.n_members, st);
   if (e != cudaSuccess) return e;
   dim3 grid(N * N / 1024, a.n_members);
-  plain_gather_kernel<<<grid, 256, 0, st>>>(a, N, psi, bits);
+  plain_gather_kernel<<<grid, 256, 0, st>>>(a, N, psi, bits, static_cast<__nv_bfloat162 *>(hi),
+                                            static_cast<__nv_bfloat162 *>(lo));
   return cudaGetLastError();
 }
 

@@ -19,7 +19,9 @@
 //   EPIE_GEMM_FP32EMU cuBLAS' fp32 emulation on bf16 tensor cores
 //   EPIE_GEMM_TC_BF16, EPIE_GEMM_TC_BF16X3: the bf16 and split-bf16 products
 //     on this engine's own tcgen05 kernel (epie_tc_gemm.cu), the three
-//     split products accumulated in one tensor-memory accumulator
+//     split products accumulated in one tensor-memory accumulator; here the
+//     splits and the transposes are folded into the gather, the GEMM
+//     epilogues and the modulus (tc_bf16_group)
 //   EPIE_GEMM_TC_TF32, EPIE_GEMM_TC_TF32X3: the same kernel on fp32 operands
 //     read as tf32 (kind::tf32); the plain form rounds its operands to the
 //     nearest tf32 first, the split form takes hi = x with its low 13
@@ -52,6 +54,8 @@ struct GemmPath {
   float *F_hi = nullptr, *F_lo = nullptr;                   // tf32 split rows, cap * N * 2N
   float2 *psi = nullptr, *Y = nullptr;                      // cap * N * N complex each
   __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;           // cap * N * 2N
+  // own tcgen05 bf16 kernel: the transposed split products of the row passes
+  __nv_bfloat16 *E_hi = nullptr, *E_lo = nullptr;           // cap * N * 2N
   double *omax = nullptr;                                   // cap
 };
 
@@ -83,7 +87,8 @@ __global__ void transpose_frames_kernel(const float2 *__restrict__ in, float2 *_
 // modulus replacement on the transposed spectrum Xt[b][kx][ky] (1/N^2 folded
 // in), error partials per 1024-element block like the plain path
 template <typename IT>
-__global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt) {
+__global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt,
+                                __nv_bfloat162 *__restrict__ hi, __nv_bfloat162 *__restrict__ lo) {
   __shared__ double se[8], ss[8];
   const int m = blockIdx.y, K = N * N;
   const int f = a.members[m];
@@ -109,7 +114,14 @@ __global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt) {
       amp = 0.f;
       v = make_float2(sq * invK, 0.f);
     }
-    Xt[static_cast<size_t>(m) * K + t] = v;
+    if (hi) {
+      // the split operand of the inverse transform, written in place of v
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+      hi[static_cast<size_t>(m) * K + t] = h;
+      if (lo) lo[static_cast<size_t>(m) * K + t] = __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
+    } else {
+      Xt[static_cast<size_t>(m) * K + t] = v;
+    }
     const float d = amp - sq;
     e = fmaf(d, d, e);
     s += In;
@@ -230,17 +242,6 @@ int rows_dft(GemmPath *g, const float2 *src, float2 *dst, long long rows, bool i
                         inverse ? g->Tit32_lo : g->Tft32_lo, dstf, mrows, n2, n2, n2, 3, err_flag,
                         st, err);
   }
-  if (tc_bf16_precision(g->precision)) {
-    const bool x3 = g->precision == EPIE_GEMM_TC_BF16X3;
-    cudaError_t e = split(srcf, g->D_hi, x3 ? g->D_lo : nullptr, rows * n2, st);
-    if (e != cudaSuccess) {
-      *err = cudaGetErrorString(e);
-      return EPIE_ECUDA;
-    }
-    return tc_gemm_bf16(g->D_hi, x3 ? g->D_lo : nullptr, inverse ? g->Tit_hi : g->Tft_hi,
-                        x3 ? (inverse ? g->Tit_lo : g->Tft_lo) : nullptr, dstf, mrows, n2, n2, n2,
-                        x3 ? 3 : 1, err_flag, st, err);
-  }
   if (g->precision == EPIE_GEMM_TF32 || g->precision == EPIE_GEMM_FP32EMU) {
     const cublasComputeType_t ct = g->precision == EPIE_GEMM_TF32
                                        ? CUBLAS_COMPUTE_32F_FAST_TF32
@@ -295,7 +296,7 @@ void gemm_path_destroy(GemmPath *g) {
   void *ptrs[] = {g->Tf,     g->Ti,     g->Tf_hi,  g->Tf_lo, g->Ti_hi, g->Ti_lo,
                   g->Tft_hi, g->Tft_lo, g->Tit_hi, g->Tit_lo, g->psi,   g->Y,
                   g->D_hi,   g->D_lo,   g->omax,   g->Tft32_hi, g->Tft32_lo, g->Tit32_hi,
-                  g->Tit32_lo, g->F_hi, g->F_lo};
+                  g->Tit32_lo, g->F_hi, g->F_lo, g->E_hi, g->E_lo};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -387,11 +388,12 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
   if (members <= g->cap) return EPIE_OK;
   int cap = members > 2 * g->cap ? members : 2 * g->cap;
   cap += cap & 1;  // even: whole 128-row blocks at N = 64
-  void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax, g->F_hi, g->F_lo};
+  void *ptrs[] = {g->psi, g->Y, g->D_hi, g->D_lo, g->omax, g->F_hi, g->F_lo, g->E_hi, g->E_lo};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->psi = g->Y = nullptr;
   g->D_hi = g->D_lo = nullptr;
+  g->E_hi = g->E_lo = nullptr;
   g->F_hi = g->F_lo = nullptr;
   g->omax = nullptr;
   g->cap = 0;
@@ -403,6 +405,11 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
     ok = cudaMalloc(&g->D_hi, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
     if (ok && x3_precision(g->precision))
       ok = cudaMalloc(&g->D_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
+  }
+  if (ok && tc_bf16_precision(g->precision)) {
+    ok = cudaMalloc(&g->E_hi, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
+    if (ok && x3_precision(g->precision))
+      ok = cudaMalloc(&g->E_lo, sizeof(__nv_bfloat16) * 2 * K * cap) == cudaSuccess;
   }
   if (ok && tc_tf32_precision(g->precision))
     ok = cudaMalloc(&g->F_hi, sizeof(float) * 2 * K * cap) == cudaSuccess;
@@ -416,11 +423,73 @@ int gemm_path_reserve(GemmPath *g, int members, std::string *err) {
   return EPIE_OK;
 }
 
+namespace {
+
+cudaError_t launch_tmodulus(const GroupArgs &a, int N, int itype, float2 *Xt, void *hi, void *lo,
+                            cudaStream_t st) {
+  dim3 grid(N * N / 1024, a.n_members);
+  auto *h = static_cast<__nv_bfloat162 *>(hi), *l = static_cast<__nv_bfloat162 *>(lo);
+  if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
+  else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
+  else tmodulus_kernel<float><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
+  return cudaGetLastError();
+}
+
+// The own tcgen05 kernel's bf16 forms, with the precision splits and the
+// transposes folded into the producers: the gather writes the split exit
+// wave; the row passes write their products transposed and split (the next
+// pass's operand); the column pass writes fp32 and the modulus writes the
+// split of its result:
+//   gather -> D ; rows(D) -> E^T ; cols(E) -> Y ; modulus(Y) -> D ;
+//   cols^-1(D) -> E^T ; rows^-1(E) -> psi' ; update.
+// Every split is bf16(v), bf16(v - bf16(v)) as in split_bf16_kernel, so the
+// result equals that of the unfolded sequence bit for bit.
+int tc_bf16_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st, std::string *err,
+                  int64_t *kernels) {
+  const int N = g->N, G = a.n_members, n2 = 2 * N;
+  const bool x3 = g->precision == EPIE_GEMM_TC_BF16X3;
+  const int terms = x3 ? 3 : 1;
+  const long long mrows = (static_cast<long long>(G) * N + 127) / 128 * 128;
+  void *dlo = x3 ? g->D_lo : nullptr, *elo = x3 ? g->E_lo : nullptr;
+  const void *tf_lo = x3 ? g->Tft_lo : nullptr, *ti_lo = x3 ? g->Tit_lo : nullptr;
+  cudaError_t e = launch_plain_gather(a, N, g->psi, g->omax, st, g->D_hi, dlo);
+  int rc = EPIE_OK;
+  if (e == cudaSuccess) {
+    if ((rc = tc_gemm_bf16_tsplit(g->D_hi, dlo, g->Tft_hi, tf_lo, g->E_hi, elo, mrows, N, n2,
+                                  terms, a.err_flag, st, err)))  // along x
+      return rc;
+    if ((rc = tc_gemm_bf16(g->E_hi, elo, g->Tft_hi, tf_lo, reinterpret_cast<float *>(g->Y), mrows,
+                           n2, n2, n2, terms, a.err_flag, st, err)))  // along y
+      return rc;
+    e = launch_tmodulus(a, N, itype, g->Y, g->D_hi, dlo, st);
+  }
+  if (e == cudaSuccess) {
+    if ((rc = tc_gemm_bf16_tsplit(g->D_hi, dlo, g->Tit_hi, ti_lo, g->E_hi, elo, mrows, N, n2,
+                                  terms, a.err_flag, st, err)))  // along y
+      return rc;
+    if ((rc = tc_gemm_bf16(g->E_hi, elo, g->Tit_hi, ti_lo, reinterpret_cast<float *>(g->psi),
+                           mrows, n2, n2, n2, terms, a.err_flag, st, err)))  // along x
+      return rc;
+    e = a.accO ? launch_mb_accumulate(a, N, g->psi, g->omax, a.accO, a.cnt, st)
+               : launch_plain_update(a, N, g->psi, g->omax, st);
+  }
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return EPIE_ECUDA;
+  }
+  // gather, modulus, update, 4 tcgen05 GEMMs
+  *kernels += 7;
+  return EPIE_OK;
+}
+
+}  // namespace
+
 int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
                     std::string *err, int64_t *kernels) {
   const int N = g->N, G = a.n_members;
   int rc = gemm_path_reserve(g, G, err);
   if (rc) return rc;
+  if (tc_bf16_precision(g->precision)) return tc_bf16_group(g, a, itype, st, err, kernels);
   const long long rows = static_cast<long long>(G) * N;
   cudaError_t e = launch_plain_gather(a, N, g->psi, g->omax, st);
   if (e != cudaSuccess) {
@@ -430,11 +499,7 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
   if ((rc = rows_dft(g, g->psi, g->Y, rows, false, a.err_flag, st, err))) return rc;   // along x
   if ((rc = transpose(g, g->Y, g->psi, G, st, err))) return rc;
   if ((rc = rows_dft(g, g->psi, g->Y, rows, false, a.err_flag, st, err))) return rc;   // along y
-  dim3 grid(N * N / 1024, G);
-  if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, g->Y);
-  else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, g->Y);
-  else tmodulus_kernel<float><<<grid, 256, 0, st>>>(a, N, g->Y);
-  if ((e = cudaGetLastError()) != cudaSuccess) {
+  if ((e = launch_tmodulus(a, N, itype, g->Y, nullptr, nullptr, st)) != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
@@ -447,6 +512,7 @@ int gemm_path_group(GemmPath *g, const GroupArgs &a, int itype, cudaStream_t st,
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
   }
+  // (the own kernel's bf16 forms took tc_bf16_group above)
   const bool split_launch = split_precision(g->precision) || tc_tf32_precision(g->precision);
   // gather, 2 transposes, modulus, update (+ 4 splits, + 4 tcgen05 GEMMs)
   *kernels += 5 + (split_launch ? 4 : 0) + (tc_precision(g->precision) ? 4 : 0);

@@ -130,9 +130,10 @@ cudaError_t launch_amp_ingest_256(const void *frames, int itype, const float *da
 cudaError_t launch_amp_ingest_512(const void *frames, int itype, const float *dark, float *amp,
                                   double *isum, int f0, int n, cudaStream_t st);
 
-// plain unfused path pieces
+// plain unfused path pieces; the gather writes psi = P . O_j (fp32), or with
+// hi set its bf16 split hi / lo (interleaved complex, lo may be null)
 cudaError_t launch_plain_gather(const GroupArgs &a, int N, float2 *psi, double *omax2,
-                                cudaStream_t st);
+                                cudaStream_t st, void *hi = nullptr, void *lo = nullptr);
 cudaError_t launch_plain_modulus(const GroupArgs &a, int N, int itype, float2 *Psi,
                                  cudaStream_t st);
 cudaError_t launch_plain_update(const GroupArgs &a, int N, const float2 *psi1,
@@ -161,6 +162,14 @@ void tc_gemm_inject(int count, long long wait_ns);
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err);
+// the same product of Nn = 2 fn columns, written for the next DFT pass: row
+// R = f fn + y of the product (row y of frame f, interleaved complex values
+// at columns 2 x + c) goes to row f fn + x, columns 2 y + c of hi (bf16 of the
+// value) and lo (bf16 of the value minus hi; lo may be null), row pitch 2 fn;
+// fn a multiple of 32 and M of fn
+int tc_gemm_bf16_tsplit(const void *A0, const void *A1, const void *B0, const void *B1, void *hi,
+                        void *lo, long long M, int fn, int K, int terms, int *err_flag,
+                        cudaStream_t st, std::string *err);
 // the same with fp32 operands read as tf32 (kind::tf32); K a multiple of 32
 int tc_gemm_tf32(const float *A0, const float *A1, const float *B0, const float *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,

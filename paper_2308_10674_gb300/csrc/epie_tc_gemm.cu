@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                    float *__restrict__ D, int ldd, int K, int terms, int m_tiles, int n_tiles,
-                   int *err_flag, uint64_t wait_ns, int inject) {
+                   int *err_flag, uint64_t wait_ns, int inject, int fn,
+                   __nv_bfloat162 *__restrict__ Thi, __nv_bfloat162 *__restrict__ Tlo) {
   using C = TcCfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   // 128-byte-swizzled tiles want 1024-byte alignment
@@ -299,6 +300,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_after();
       const int m0 = (tile / n_tiles) * TC_BM, n0 = (tile % n_tiles) * BN;
       const uint32_t tq = tmem + static_cast<uint32_t>(b * BN) + (static_cast<uint32_t>(32 * q) << 16);
+      if (Thi) {
+        // transposed split output: row R = f fn + y of D holds the row y of
+        // frame f as interleaved complex values (column 2 x + c); it goes to
+        // row f fn + x, column 2 y + c of the next GEMM's operand, as
+        // hi = bf16(v) and lo = bf16(v - hi).  Lane l holds row y0 + l, so for
+        // each x the warp's stores are 32 consecutive 4-byte (re, im) pairs.
+        const long long R = static_cast<long long>(m0) + 32 * q + lane;
+        const long long fr = R / fn;
+        const int y = static_cast<int>(R - fr * fn);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(tq + c, r);
+          const long long row0 = fr * fn + ((n0 + c) >> 1);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+            const size_t o = static_cast<size_t>(row0 + j) * fn + y;  // in (re, im) pairs
+            Thi[o] = h;
+            if (Tlo) Tlo[o] = __floats2bfloat162_rn(re - __low2float(h), im - __high2float(h));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
+        continue;
+      }
       // lane l holds row l of the warp's 32 rows; through the staging tile,
       // lanes 8i..8i+7 then store 128 contiguous bytes of one row
       float *stg = reinterpret_cast<float *>(smem + C::OFF_STG + (warp - 2) * C::STG_BYTES);
@@ -380,9 +409,18 @@ bool make_map(CUtensorMap *m, const void *base, long long rows, int K, int box_r
   return true;
 }
 
+// where the product goes: fp32 D (row pitch ldd), or, when thi is set, the
+// rows of frames of side fn transposed and split into bf16 hi / lo pairs
+struct TcOut {
+  float *D = nullptr;
+  int ldd = 0;
+  int fn = 0;
+  __nv_bfloat162 *thi = nullptr, *tlo = nullptr;
+};
+
 template <int BN, bool TF32>
 cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                      const CUtensorMap &b1, float *D, long long M, int Nn, int K, int ldd,
+                      const CUtensorMap &b1, const TcOut &out, long long M, int Nn, int K,
                       int terms, int *err_flag, uint64_t wait_ns, int inject, cudaStream_t st) {
   using C = TcCfg<BN>;
   static int attr_dev = -1, sms = 0;
@@ -399,29 +437,38 @@ cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtens
   const int m_tiles = static_cast<int>(M / TC_BM), n_tiles = Nn / BN;
   const long long tiles = static_cast<long long>(m_tiles) * n_tiles;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);  // one CTA per SM
-  tc_gemm_kernel<BN, TF32><<<grid, TC_THREADS, C::SMEM, st>>>(a0, a1, b0, b1, D, ldd, K, terms,
-                                                                m_tiles, n_tiles, err_flag, wait_ns,
-                                                                inject);
+  tc_gemm_kernel<BN, TF32><<<grid, TC_THREADS, C::SMEM, st>>>(
+      a0, a1, b0, b1, out.D, out.ldd, K, terms, m_tiles, n_tiles, err_flag, wait_ns, inject,
+      out.fn, out.thi, out.tlo);
   return cudaGetLastError();
 }
 
-int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, float *D, long long M,
-            int Nn, int K, int ldd, int terms, bool tf32, int *err_flag, cudaStream_t st,
+int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, const TcOut &out,
+            long long M, int Nn, int K, int terms, bool tf32, int *err_flag, cudaStream_t st,
             std::string *err) {
   const int BN = Nn % 256 == 0 ? 256 : 128;
   const int bk = tf32 ? TcElem<true>::BK : TcElem<false>::BK;
-  if (!A0 || !B0 || !D || !err_flag || (terms != 1 && terms != 3) ||
+  const bool split = out.thi != nullptr;
+  if (!A0 || !B0 || (!split && !out.D) || !err_flag || (terms != 1 && terms != 3) ||
       (terms == 3 && (!A1 || !B1))) {
     *err = "null operand, or terms not 1 or 3";
     return EPIE_EINVAL;
   }
-  if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % bk || ldd < Nn || ldd % 4 ||
-      (M / TC_BM) * (Nn / 128) > 0x7fffffffLL) {
+  if (M <= 0 || M % TC_BM || Nn <= 0 || Nn % 128 || K <= 0 || K % bk ||
+      (!split && (out.ldd < Nn || out.ldd % 4)) || (M / TC_BM) * (Nn / 128) > 0x7fffffffLL) {
     *err = "M must be a positive multiple of 128, Nn of 128, K of " + std::to_string(bk) +
            "; ldd >= Nn and a multiple of 4";
     return EPIE_EINVAL;
   }
-  const void *ptrs[5] = {A0, A1 ? A1 : A0, B0, B1 ? B1 : B0, D};
+  // transposed output: whole frames of side fn (a multiple of 32, so a
+  // warp's 32 rows lie in one frame), rows of 2 fn values
+  if (split && (tf32 || out.fn < 32 || out.fn % 32 || Nn != 2 * out.fn || M % out.fn)) {
+    *err = "transposed output: bf16 operands, frame side a multiple of 32, Nn = 2 fn, M = frames x fn";
+    return EPIE_EINVAL;
+  }
+  const void *dst = split ? static_cast<const void *>(out.thi) : static_cast<const void *>(out.D);
+  const void *dst2 = split && out.tlo ? static_cast<const void *>(out.tlo) : dst;
+  const void *ptrs[6] = {A0, A1 ? A1 : A0, B0, B1 ? B1 : B0, dst, dst2};
   for (const void *p : ptrs)
     if (reinterpret_cast<uintptr_t>(p) % 16) {
       *err = "operands must be 16-byte aligned";
@@ -442,11 +489,11 @@ int tc_gemm(const void *A0, const void *A1, const void *B0, const void *B1, floa
     }
   cudaError_t e;
   if (tf32)
-    e = BN == 256 ? launch_tc<256, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st)
-                  : launch_tc<128, true>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st);
+    e = BN == 256 ? launch_tc<256, true>(a0, a1, b0, b1, out, M, Nn, K, terms, err_flag, w, inj, st)
+                  : launch_tc<128, true>(a0, a1, b0, b1, out, M, Nn, K, terms, err_flag, w, inj, st);
   else
-    e = BN == 256 ? launch_tc<256, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st)
-                  : launch_tc<128, false>(a0, a1, b0, b1, D, M, Nn, K, ldd, terms, err_flag, w, inj, st);
+    e = BN == 256 ? launch_tc<256, false>(a0, a1, b0, b1, out, M, Nn, K, terms, err_flag, w, inj, st)
+                  : launch_tc<128, false>(a0, a1, b0, b1, out, M, Nn, K, terms, err_flag, w, inj, st);
   if (e != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return EPIE_ECUDA;
@@ -464,13 +511,33 @@ void tc_gemm_inject(int count, long long wait_ns) {
 int tc_gemm_bf16(const void *A0, const void *A1, const void *B0, const void *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err) {
-  return tc_gemm(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, false, err_flag, st, err);
+  TcOut out;
+  out.D = D;
+  out.ldd = ldd;
+  return tc_gemm(A0, A1, B0, B1, out, M, Nn, K, terms, false, err_flag, st, err);
+}
+
+int tc_gemm_bf16_tsplit(const void *A0, const void *A1, const void *B0, const void *B1, void *hi,
+                        void *lo, long long M, int fn, int K, int terms, int *err_flag,
+                        cudaStream_t st, std::string *err) {
+  TcOut out;
+  out.fn = fn;
+  out.thi = static_cast<__nv_bfloat162 *>(hi);
+  out.tlo = static_cast<__nv_bfloat162 *>(lo);
+  if (!hi) {
+    *err = "null output";
+    return EPIE_EINVAL;
+  }
+  return tc_gemm(A0, A1, B0, B1, out, M, 2 * fn, K, terms, false, err_flag, st, err);
 }
 
 int tc_gemm_tf32(const float *A0, const float *A1, const float *B0, const float *B1, float *D,
                  long long M, int Nn, int K, int ldd, int terms, int *err_flag, cudaStream_t st,
                  std::string *err) {
-  return tc_gemm(A0, A1, B0, B1, D, M, Nn, K, ldd, terms, true, err_flag, st, err);
+  TcOut out;
+  out.D = D;
+  out.ldd = ldd;
+  return tc_gemm(A0, A1, B0, B1, out, M, Nn, K, terms, true, err_flag, st, err);
 }
 
 }  // namespace epie
