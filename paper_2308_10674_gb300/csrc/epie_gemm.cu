@@ -85,25 +85,39 @@ __global__ void transpose_frames_kernel(const float2 *__restrict__ in, float2 *_
 }
 
 // modulus replacement on the transposed spectrum Xt[b][kx][ky] (1/N^2 folded
-// in), error partials per 1024-element block like the plain path
+// in), or (hi set) its bf16 split written instead.  One block per 32 x 32
+// tile (kx0, ky0) of a member: the intensities, stored [ky][kx], are read
+// along kx into shared memory and used along ky, so both the frame and the
+// spectrum are read in whole rows; error partials per tile (N^2 / 1024 per
+// frame, the plain path's slots)
 template <typename IT>
 __global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt,
                                 __nv_bfloat162 *__restrict__ hi, __nv_bfloat162 *__restrict__ lo) {
+  __shared__ float sI[32][33];
   __shared__ double se[8], ss[8];
-  const int m = blockIdx.y, K = N * N;
+  const int m = blockIdx.z, K = N * N, tx = threadIdx.x, ty = threadIdx.y;
+  const int kx0 = 32 * blockIdx.x, ky0 = 32 * blockIdx.y;
   const int f = a.members[m];
   const IT *I = static_cast<const IT *>(a.frames) + static_cast<size_t>(f) * K;
   const float invK = 1.0f / (static_cast<float>(N) * static_cast<float>(N));
-  float e = 0.f, s = 0.f;
+  float s = 0.f;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int t = blockIdx.x * 1024 + r * 256 + threadIdx.x;  // index in Xt: kx * N + ky
-    const int kx = t / N, ky = t % N;
-    float In = ival(I[ky * N + kx]);
-    if (a.dark) In -= a.dark[ky * N + kx];
+    const int ky = ky0 + ty + 8 * r, k = ky * N + kx0 + tx;
+    float In = ival(I[k]);
+    if (a.dark) In -= a.dark[k];
     In = fmaxf(In, 0.f);
+    sI[ty + 8 * r][tx] = In;
+  }
+  __syncthreads();
+  float e = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int kx = kx0 + ty + 8 * r, ky = ky0 + tx;
+    const size_t t = static_cast<size_t>(m) * K + static_cast<size_t>(kx) * N + ky;
+    const float In = sI[tx][ty + 8 * r];
     const float sq = sqrtf(In);
-    float2 v = Xt[static_cast<size_t>(m) * K + t];
+    float2 v = Xt[t];
     const float a2 = v.x * v.x + v.y * v.y;
     float amp;
     if (a2 > 0.f) {
@@ -117,29 +131,31 @@ __global__ void tmodulus_kernel(GroupArgs a, int N, float2 *__restrict__ Xt,
     if (hi) {
       // the split operand of the inverse transform, written in place of v
       const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-      hi[static_cast<size_t>(m) * K + t] = h;
-      if (lo) lo[static_cast<size_t>(m) * K + t] = __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
+      hi[t] = h;
+      if (lo) lo[t] = __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
     } else {
-      Xt[static_cast<size_t>(m) * K + t] = v;
+      Xt[t] = v;
     }
     const float d = amp - sq;
     e = fmaf(d, d, e);
     s += In;
   }
+  const int w = (ty * 32 + tx) >> 5;
   const float we = warp_sum_f(e), ws = warp_sum_f(s);
-  if ((threadIdx.x & 31) == 0) {
-    se[threadIdx.x >> 5] = we;
-    ss[threadIdx.x >> 5] = ws;
+  if (tx == 0) {
+    se[w] = we;
+    ss[w] = ws;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tx == 0 && ty == 0) {
     double te = 0.0, ts = 0.0;
-    for (int w = 0; w < 8; ++w) {
-      te += se[w];
-      ts += ss[w];
+    for (int q = 0; q < 8; ++q) {
+      te += se[q];
+      ts += ss[q];
     }
-    a.err_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = te;
-    a.isum_part[static_cast<size_t>(f) * a.err_stride + blockIdx.x] = ts;
+    const int slot = blockIdx.y * (N / 32) + blockIdx.x;
+    a.err_part[static_cast<size_t>(f) * a.err_stride + slot] = te;
+    a.isum_part[static_cast<size_t>(f) * a.err_stride + slot] = ts;
   }
 }
 
@@ -427,11 +443,11 @@ namespace {
 
 cudaError_t launch_tmodulus(const GroupArgs &a, int N, int itype, float2 *Xt, void *hi, void *lo,
                             cudaStream_t st) {
-  dim3 grid(N * N / 1024, a.n_members);
+  dim3 grid(N / 32, N / 32, a.n_members), block(32, 8);
   auto *h = static_cast<__nv_bfloat162 *>(hi), *l = static_cast<__nv_bfloat162 *>(lo);
-  if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
-  else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
-  else tmodulus_kernel<float><<<grid, 256, 0, st>>>(a, N, Xt, h, l);
+  if (itype == EPIE_U16) tmodulus_kernel<uint16_t><<<grid, block, 0, st>>>(a, N, Xt, h, l);
+  else if (itype == EPIE_F16) tmodulus_kernel<__half><<<grid, block, 0, st>>>(a, N, Xt, h, l);
+  else tmodulus_kernel<float><<<grid, block, 0, st>>>(a, N, Xt, h, l);
   return cudaGetLastError();
 }
 
