@@ -372,8 +372,7 @@ __global__ void mb_accumulate_kernel(GroupArgs a, int N, const float2 *__restric
     const float2 o = a.O[oi], p = a.P[i];
     const float2 d = csub(psi1[static_cast<size_t>(m) * K + i], cmul(p, o));
     const float2 uo = cscale(cmulc(p, d), ao), up = cmulc(o, d);
-    atomicAdd(&accO[oi].x, uo.x);
-    atomicAdd(&accO[oi].y, uo.y);
+    atomicAdd(accO + oi, uo);  // one paired (8-byte) atomic
     atomicAdd(cnt + oi, 1);
     a.probe_part[static_cast<size_t>(m) * K + i] = cscale(up, bp);
   }

@@ -466,8 +466,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<CL, NT>()) epie_fused_ker
       const float2 d = csub(psi1, cmul(p, o));
       const float2 uo = cscale(cmulc(p, d), inv_pm);
       const size_t oi = obase + y * orow + xl;
-      atomicAdd(&a.accO[oi].x, uo.x);
-      atomicAdd(&a.accO[oi].y, uo.y);
+      atomicAdd(a.accO + oi, uo);  // one paired (8-byte) atomic
       atomicAdd(a.cnt + oi, 1);
       part[y * N + xl] = cscale(cmulc(o, d), bp);
     }

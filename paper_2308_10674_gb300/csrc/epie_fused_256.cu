@@ -513,8 +513,7 @@ __global__ void __launch_bounds__(S_NT, 2) epie_fused256_kernel(GroupArgs a) {
           const float2 d = csub(v[r], cmul(p, o));
           const float2 uo = cscale(cmulc(p, d), inv_pm);
           const size_t oi = obase + static_cast<size_t>(16 * r) * orow;
-          atomicAdd(&a.accO[oi].x, uo.x);
-          atomicAdd(&a.accO[oi].y, uo.y);
+          atomicAdd(a.accO + oi, uo);  // one paired (8-byte) atomic
           atomicAdd(a.cnt + oi, 1);
           part[16 * r * S_N] = cscale(cmulc(o, d), bp);
         }
