@@ -72,6 +72,8 @@ def parse():
                          "the FP64 oracle on one host core and on all of them (no GPU); "
                          "parallel: the paper's disjoint-subset averaging scheme; gemm-path: "
                          "the DFT-as-GEMM path at every operand precision against the FFT path")
+    ap.add_argument("--gemm-variant", default=None,
+                    help="gemm-path: run only this variant (e.g. \"tc bf16x3\") at --frame-side")
     ap.add_argument("--sweeps-per-chunk", type=int, default=50,
                     help="live-schedule: sweeps after each chunk (and at the end)")
     return ap.parse_args()
@@ -914,9 +916,15 @@ def run_gemm_path(args):
          ("tc bf16x3", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_BF16X3),
          ("tc tf32", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_TF32),
          ("tc tf32x3", B.EPIE_PATH_GEMM, B.EPIE_GEMM_TC_TF32X3)]
+    sides = (128, 256)
+    if args.gemm_variant is not None:
+        V = [v for v in V if v[0] == args.gemm_variant]
+        if not V:
+            raise SystemExit(f"unknown --gemm-variant {args.gemm_variant!r}")
+        sides = (args.frame_side,)
     rows = []
     with Clocks(0) as clk:
-        for N in (128, 256):
+        for N in sides:
             n = 16384
             d = synth.live_scan(N=N, n=n, geometry="B", seed=0, workers=args.workers,
                                 fwhm=60.0 * N / 256)
@@ -934,7 +942,7 @@ def run_gemm_path(args):
                 eng.close()
                 rows.append({"N": N, "path": name, "frame_updates_per_s": n / dt,
                              "ms_per_sweep": dt * 1e3, "sweep_error": float(errs[-1])})
-    ref = [r for r in rows if r["N"] == 256 and r["path"] == "tc bf16x3"][0]
+    ref = ([r for r in rows if r["N"] == 256 and r["path"] == "tc bf16x3"] or rows)[0]
     line = {"metric": "DFT-as-GEMM ePIE frame-updates/s at 256^2 (tcgen05 split bf16), "
                       "mini-batch B = 1024",
             "value": ref["frame_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
