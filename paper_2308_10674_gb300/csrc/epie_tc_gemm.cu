@@ -25,7 +25,9 @@
 //   * two BN-column accumulators alternate in tensor memory; after a tile's
 //     last k-block a commit completes "acc_full[b]", warps 2-5 read the rows
 //     of their TMEM lane quadrant with tcgen05.ld.32x32b, stage them through
-//     shared memory and store whole 128-byte row segments, then arrive on
+//     shared memory and store whole 128-byte row segments (or, for the DFT
+//     path's row passes, store the product of whole frames transposed and
+//     split into bf16 hi / lo straight from the registers), then arrive on
 //     "acc_empty[b]", while the MMAs of the next tile run.
 // Every wait is bounded by %globaltimer (2 s).  On expiry the kernel sets
 // FLAG_TC_TIMEOUT in the status word, stops, lets its issued copies land and
