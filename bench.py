@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--path", default="fused", choices=["fused", "plain"])
     ap.add_argument("--graph", action="store_true",
                     help="replay each sweep's launches from a captured CUDA graph")
+    ap.add_argument("--ctas-per-frame", type=int, default=0,
+                    help="fused path: the step kernel's tile shape (0: the default for the "
+                         "frame side; 1, 2 or 4 at 128^2)")
     ap.add_argument("--class-cap", type=int, default=0,
                     help="at most this many frames per colour class (0: no cap)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
@@ -315,7 +318,8 @@ def run_ours(args):
     def make_engine(p=path, cap=n):
         eng = B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=cap, mode=B.EPIE_COLOURED,
                        path=p, seed=5, device=device, stream=stream.cuda_stream,
-                       class_cap=args.class_cap, flags=B.EPIE_GRAPH if args.graph else 0)
+                       class_cap=args.class_cap, flags=B.EPIE_GRAPH if args.graph else 0,
+                       ctas_per_frame=args.ctas_per_frame if p == B.EPIE_PATH_FUSED else 0)
         eng.set_dark(d["dark"])
         return eng
 
@@ -443,6 +447,7 @@ def run_ours(args):
                        "object": [d["H"], d["W"]], "colour_classes": n_classes,
                        "geometry": args.geometry, "path": args.path,
                        "class_cap": args.class_cap, "graph_replay": bool(args.graph),
+                       "ctas_per_frame": args.ctas_per_frame,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (frame set %.2f GB)" % (frames.nbytes / 1e9),
                        "sweep_error_last": errs[-1]},

@@ -161,9 +161,9 @@ typedef struct {
                               class (first-fit skips full classes); 0 = no cap  */
   int32_t gemm_precision;  /* EPIE_PATH_GEMM: EPIE_GEMM_*                        */
   int32_t ctas_per_frame;  /* EPIE_PATH_FUSED, the step kernel's tile shape: CTAs
-                              (one cluster) per frame; 0 = the default (1, 1, 8,
+                              (one cluster) per frame; 0 = the default (1, 4, 8,
                               16 for N = 64, 128, 256, 512); N = 128 also builds
-                              2 and 4 (see the autotuner)                       */
+                              1 and 2 (see the autotuner)                       */
 } epie_config;
 
 /* Fills *cfg with defaults: N 256, object 1024^2, capacity 1024, EPIE_U16,

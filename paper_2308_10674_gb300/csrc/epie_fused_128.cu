@@ -1,5 +1,5 @@
 // epie_fused_128.cu -- the fused ePIE position-update kernels for 128 x 128
-// frames, in three tile shapes: 1 (the default), 2 or 4 CTAs per frame.
+// frames, in three tile shapes: 1, 2 or 4 (the default) CTAs per frame.
 //
 // The 1-CTA shape is its own kernel: one CTA of 1024 threads owns one scan
 // position of a group (the ePIE step of Maiden & Rodenburg 2009, as the
@@ -30,7 +30,9 @@
 // warp-uniform.
 //
 // The 2- and 4-CTA shapes are the general kernel of epie_fused.cuh; they
-// read the amplitudes in plain FFT order.
+// read the amplitudes in plain FFT order.  Spreading a frame over 4 SMs
+// shortens the step of a small colour class (tens of frames), so 4 is the
+// default; one CTA per frame suits large groups (mini-batches of hundreds).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -591,9 +593,17 @@ cudaError_t launch_fused_128(int itype, const GroupArgs &a, cudaStream_t st, int
   }
 }
 
-size_t fused_smem_128(int /*itype*/) {
-  static_assert(EPIE_CTAS_128 == 1, "the default 128^2 shape is the 1-CTA kernel");
-  return SMEM128;
+size_t fused_smem_128(int itype) {
+  // the default shape's shared memory (EPIE_CTAS_128 CTAs per frame)
+  constexpr int CL = EPIE_CTAS_128;
+  if constexpr (CL == 1) {
+    return SMEM128;
+  } else {
+    constexpr int NT = 128 * 128 / (CL * 16);
+    if (itype == 0) return FusedCfg<128, CL, NT, uint16_t>::SMEM;
+    if (itype == 1) return FusedCfg<128, CL, NT, __half>::SMEM;
+    return FusedCfg<128, CL, NT, float>::SMEM;
+  }
 }
 
 cudaError_t launch_amp_ingest_128(const void *frames, int itype, const float *dark, float *amp,

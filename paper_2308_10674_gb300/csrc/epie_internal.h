@@ -13,7 +13,7 @@
 #define EPIE_CTAS_64 1
 #endif
 #ifndef EPIE_CTAS_128
-#define EPIE_CTAS_128 1
+#define EPIE_CTAS_128 4
 #endif
 #ifndef EPIE_CTAS_256
 #define EPIE_CTAS_256 8

@@ -4,8 +4,9 @@ bench.py's multiscan leg, generated the same way): the 128^2 and 512^2 step
 kernels on the full objects of their scans, through the engine (amplitudes
 derived at append, the engine's own colouring and order).
 
-* One whole colour class of the 128^2 spiral scan (9,000 positions) and of
-  the 512^2 raster scan (1,024 positions), against the FP64 oracle from a
+* One whole colour class of the 128^2 spiral scan (9,000 positions; the
+  1-CTA kernel and the default 4-CTA shape) and of the 512^2 raster scan
+  (1,024 positions), against the FP64 oracle from a
   textured start: one dependent step, so the comparison is sharp, on the
   state, the increment and the sweep error.
 * Two mini-batches of 8 overlapping positions of the 512^2 spiral scan (8,000
@@ -41,8 +42,8 @@ def multiscan(i):
     return N, d, O0.astype(np.complex64), P0.astype(np.complex64)
 
 
-@pytest.mark.parametrize("scan", [2, 5])
-def test_class_on_the_full_object(orc, scan):
+@pytest.mark.parametrize("scan,shape", [(2, 1), (2, 0), (5, 0)])
+def test_class_on_the_full_object(orc, scan, shape):
     N, d, O0, P0 = multiscan(scan)
     col, ncls = orc.colour_greedy(d["pos"], N)
     order, gs = orc.order_coloured(5, 0, col, ncls)
@@ -50,7 +51,7 @@ def test_class_on_the_full_object(orc, scan):
     sel = order[gs[g]:gs[g + 1]]
     frames, pos = d["frames"][sel], np.ascontiguousarray(d["pos"][sel])
     with B.Engine(N, d["H"], d["W"], P0, O0, capacity=len(sel), mode=B.EPIE_COLOURED, seed=5,
-                  device=0, intensity_dtype=B.EPIE_F16) as eng:
+                  device=0, intensity_dtype=B.EPIE_F16, ctas_per_frame=shape) as eng:
         eng.append(frames, pos)
         assert eng.n_classes == 1
         e_g = eng.iterate(1)

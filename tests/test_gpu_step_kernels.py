@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
 # per frame side: (types: raster ny, nx, step, seed), (graph: step, seed),
 # (sequential: step, seed), (mini-batch: step, seed), (one large class: side
 # of the disjoint raster, its frames exceed one wave)
+# the tile shape each test asks for: the 1-CTA kernel at 128^2 (the default
+# 128^2 shape is the general kernel's 4-CTA clusters), the default at 512^2
+SHAPE = {128: 1, 512: 0}
+
 INSTANCES = {
     128: dict(types=(1, 3, 75, 21), graph=(65, 128), seq=(50, 25), mb=(50, 23), wave=13),
     512: dict(types=(1, 3, 300, 21), graph=(260, 512), seq=(200, 25), mb=(200, 23), wave=4),
@@ -39,7 +43,7 @@ def test_types_dark_and_raw_rows(orc, N, dtype, code, raw):
     d = synth.small_scan(N, ny, nx, step, seed=seed, dark=True, photons=1e7, dtype=dtype)
     st = textured_start(d)
     O, P, e = sharp(orc, d, B.EPIE_COLOURED, st)
-    with engine(d, B.EPIE_COLOURED, st, intensity_dtype=code,
+    with engine(d, B.EPIE_COLOURED, st, ctas_per_frame=SHAPE[N], intensity_dtype=code,
                 flags=B.EPIE_RAW_INTENSITY if raw else 0) as eng:
         eng.set_dark(d["dark"])
         eng.append(d["frames"], d["pos"])
@@ -56,7 +60,7 @@ def test_group_larger_than_a_wave(orc, N):
     d = synth.small_scan(N, s, s, N + 2, seed=22, jitter=0, margin=2, photons=1e7)
     st = textured_start(d)
     O, P, e = oracle_run(orc, d, B.EPIE_COLOURED, 1, st)
-    with engine(d, B.EPIE_COLOURED, st) as eng:
+    with engine(d, B.EPIE_COLOURED, st, ctas_per_frame=SHAPE[N]) as eng:
         eng.append(d["frames"], d["pos"])
         assert eng.n_classes == 1
         e_g = eng.iterate(1)
@@ -79,7 +83,7 @@ def test_minibatch(orc, N, batch):
 
     (O, P, e), sp = spread(run, st)
     assert max(sp[:2]) <= WELL_CONDITIONED, sp
-    with engine(d, B.EPIE_MINIBATCH, st, batch=batch) as eng:
+    with engine(d, B.EPIE_MINIBATCH, st, ctas_per_frame=SHAPE[N], batch=batch) as eng:
         eng.append(d["frames"], d["pos"])
         assert np.array_equal(eng.order(0)[0], order)
         e_g = eng.iterate(1)
@@ -94,7 +98,8 @@ def test_graph_replay_and_global_object_max(orc, N):
     d = synth.small_scan(N, 2, 3, step, seed=seed)
     st = textured_start(d)
     O, P, e = sharp(orc, d, B.EPIE_COLOURED, st, n_sweeps=2, omax_global=True)
-    with engine(d, B.EPIE_COLOURED, st, flags=B.EPIE_GRAPH, omax_mode=B.EPIE_OMAX_GLOBAL) as eng:
+    with engine(d, B.EPIE_COLOURED, st, ctas_per_frame=SHAPE[N], flags=B.EPIE_GRAPH,
+                omax_mode=B.EPIE_OMAX_GLOBAL) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(2)
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)
@@ -106,7 +111,7 @@ def test_sequential(orc, N):
     d = synth.small_scan(N, 2, 2, step, seed=seed)
     st = textured_start(d)
     O, P, e = sharp(orc, d, B.EPIE_SEQUENTIAL, st)
-    with engine(d, B.EPIE_SEQUENTIAL, st) as eng:
+    with engine(d, B.EPIE_SEQUENTIAL, st, ctas_per_frame=SHAPE[N]) as eng:
         eng.append(d["frames"], d["pos"])
         e_g = eng.iterate(1)
         assert_parity(eng.object(), eng.probe(), e_g, O, P, e, start=st)

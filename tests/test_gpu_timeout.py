@@ -19,14 +19,15 @@ pytestmark = pytest.mark.gpu
 WAIT_NS = 1_000_000  # 1 ms
 
 
-@pytest.mark.parametrize("N,ny,nx,step", [(64, 3, 3, 33), (128, 3, 3, 65), (256, 2, 3, 130),
-                                           (512, 2, 2, 260)])
-def test_step_kernel_wait_expiry_is_reported(N, ny, nx, step):
+@pytest.mark.parametrize("N,ny,nx,step,shape", [(64, 3, 3, 33, 0), (128, 3, 3, 65, 0),
+                                                 (128, 3, 3, 65, 1), (256, 2, 3, 130, 0),
+                                                 (512, 2, 2, 260, 0)])
+def test_step_kernel_wait_expiry_is_reported(N, ny, nx, step, shape):
     d = synth.small_scan(N, ny, nx, step, seed=31)
 
     def engine():
         return B.Engine(N, d["H"], d["W"], d["P0"], None, capacity=len(d["pos"]),
-                        mode=B.EPIE_COLOURED, seed=5, device=0)
+                        mode=B.EPIE_COLOURED, seed=5, device=0, ctas_per_frame=shape)
 
     with engine() as eng:
         eng.append(d["frames"], d["pos"])
