@@ -23,7 +23,7 @@
  *     every sweep covers the frames present when it starts.
  *   - Parallel averaging over disjoint subsets (Sec. "Simulating live and
  *     parallel processing") is composed from these sweeps in oracle.py.
- * Readings where the paper is silent (each one is also listed in the design doc):
+ * Readings where the paper is silent (the engine takes the same ones):
  *   R1 F is the unnormalised DFT with exp(-2 pi i k.r/N); F^-1 carries 1/N^2.
  *      Frames arrive DC-centred; the DC moves to index 0 by ifftshift.
  *   R2 u(0) = 1: at |Psi| = 0 the replaced value is sqrt(I).

@@ -1,6 +1,6 @@
 """Degenerate and extreme inputs of the step, through the C ABI, against the
 FP64 oracle (paper, Sec. "ePIE Implementation": ePIE's projections; the
-readings R2 and R4 of the design notes):
+readings R2 and R4 of the oracle, oracle/epie_oracle.c):
 
 * a probe of zeros: the exit wave and its far field vanish everywhere, so
   every replaced value is sqrt(I) (u(0) = 1), max|P|^2 = 0 turns the object

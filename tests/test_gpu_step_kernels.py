@@ -5,7 +5,7 @@ oracle through the C ABI, in every branch they have: derived amplitudes and
 raw rows of each intensity type with a dark field, the mini-batch
 instantiation, a group larger than one wave, graph replay from the device
 group table, and the global object maximum (paper, Sec. "ePIE
-Implementation"; readings R4, R5, R7 of the design notes).  Sharp parity:
+Implementation"; readings R4, R5, R7 of the oracle, oracle/epie_oracle.c).  Sharp parity:
 one sweep from a textured start, on instances whose oracle moves by less
 than 1e-6 under a 1e-7 perturbation of its start probe."""
 import numpy as np
