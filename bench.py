@@ -110,6 +110,19 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def step_kernel_name(N, ctas_per_frame=0):
+    """The fused step kernel that runs at frame side N and tile shape
+    ctas_per_frame (0: the default shape)."""
+    if N == 256:
+        return "epie_fused256_kernel"
+    if N == 512:
+        return "epie_fused512_kernel"
+    if N == 128:
+        cl = ctas_per_frame or 4
+        return "epie_fused128_kernel" if cl == 1 else f"epie_fused_kernel<128,{cl},...>"
+    return f"epie_fused_kernel<{N},1,...>"
+
+
 def measured_traffic():
     """DRAM bytes per frame of the fused 256^2 kernel from the committed ncu
     summary (key: value lines), if it was taken on the current kernel source
@@ -412,7 +425,8 @@ def run_ours(args):
     achieved = flops_per_launch / (kernel_avg_ms / 1e3) / 1e12
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    tr = measured_traffic() if N == 256 else None
+    fused = args.path == "fused"
+    tr = measured_traffic() if (N == 256 and fused) else None
     traffic = None if tr is None else tr["dram_bytes_per_frame"] * frames_per_launch
     hbm_bytes_per_frame = N * N * 4  # the frame's fp32 measured-amplitude tile
     hbm_achieved = hbm_bytes_per_frame * frames_per_launch / (kernel_avg_ms / 1e3) / 1e9
@@ -425,7 +439,8 @@ def run_ours(args):
         fma = {"unavailable": str(ex)}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                 "frac": achieved / peak_fp32, "traffic": traffic,
-                "kernel": f"epie_fused_kernel<{N},...>",
+                "kernel": step_kernel_name(N, args.ctas_per_frame) if fused else
+                          "plain path group (gather, cuFFT, modulus, cuFFT, update)",
                 "flops_per_frame": fft_flops(N), "frames_per_launch": frames_per_launch,
                 "avg_launch_ms": kernel_avg_ms, "launches": k_launches,
                 "peak_note": (f"FP32 FMA peak = {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 "

@@ -40,3 +40,11 @@ def test_committed_traffic_record_parses():
 def test_replica_rate_single_process():
     value, secs = bench.replica_rate(1000, 2.0)
     assert value == pytest.approx(500.0) and secs == pytest.approx(2.0)
+
+
+def test_step_kernel_names_follow_frame_side_and_tile_shape():
+    assert bench.step_kernel_name(256) == "epie_fused256_kernel"
+    assert bench.step_kernel_name(512) == "epie_fused512_kernel"
+    assert bench.step_kernel_name(128) == "epie_fused_kernel<128,4,...>"
+    assert bench.step_kernel_name(128, 1) == "epie_fused128_kernel"
+    assert bench.step_kernel_name(64) == "epie_fused_kernel<64,1,...>"
