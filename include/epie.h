@@ -341,7 +341,7 @@ EPIE_API int epie_kernel_timing(epie_t h, int64_t *launches, double *ms, int64_t
  * positions and disjointness are checked on the device before the step
  * (EPIE_EINVAL / EPIE_ERANGE).  The first call on a device looks the array's
  * device address up, uploads the twiddle tables and waits for the device to
- * finish that upload; make that first call before any stream capture begins.
+ * finish that upload.
  * On failure epie_error(NULL) holds the reason. */
 EPIE_API int epie_group_step_static(int32_t N, int32_t intensity_dtype, float *object,
                                     int32_t obj_h, int32_t obj_w, float *probe,

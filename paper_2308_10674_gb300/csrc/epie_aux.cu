@@ -7,6 +7,7 @@
 
 #include "../../include/epie.h"
 #include "epie_fft.cuh"
+#include "epie_ingest.cuh"
 #include "epie_internal.h"
 
 namespace epie {
@@ -479,32 +480,56 @@ cudaError_t launch_fill(float2 *p, long long n, float2 v, cudaStream_t st) {
 
 namespace {
 // Measured amplitude of frames [f0, f0 + n) in FFT order: amp = sqrt(max(I -
-// dark, 0)), and the frame's sum of max(I - dark, 0) (error-free FP32 per thread, FP64
-// across threads).  One block per
-// frame; each thread sums a fixed set of elements and the block adds the
-// thread sums in a fixed order, so the sums do not depend on scheduling.
+// dark, 0)), and the frame's sum of max(I - dark, 0) (error-free FP32 per
+// thread, FP64 across threads).  One block per frame; each thread takes
+// chunks of 8 consecutive elements, loads up to AI_U chunks as 16-byte
+// vectors before converting any, and writes each chunk as two float4.  Each
+// thread sums a fixed set of elements and the block adds the thread sums in
+// a fixed order, so the sums do not depend on scheduling.
+constexpr int AI_NT = 512, AI_U = 4;
 template <typename IT>
-__global__ void __launch_bounds__(1024) amp_ingest_kernel(const IT *__restrict__ frames,
-                                                         const float *__restrict__ dark,
-                                                         float *__restrict__ amp,
-                                                         double *__restrict__ isum, int f0, int K) {
-  __shared__ double sh[1024];
+__global__ void __launch_bounds__(AI_NT) amp_ingest_kernel(const IT *__restrict__ frames,
+                                                          const float *__restrict__ dark,
+                                                          float *__restrict__ amp,
+                                                          double *__restrict__ isum, int f0, int K) {
+  __shared__ double sh[AI_NT];
   const size_t base = static_cast<size_t>(f0 + blockIdx.x) * K;
+  const IT *fr = frames + base;
+  float *out = amp + base;
+  const int t = threadIdx.x, nc = K >> 3;  // K is a multiple of 8
   float s = 0.f, cc = 0.f;  // error-free FP32 sum (the FP64 pipe is narrow)
-  for (int i = threadIdx.x; i < K; i += 1024) {
-    float v = ival(frames[base + i]);
-    if (dark) v -= dark[i];
-    v = fmaxf(v, 0.f);
-    two_sum_add(s, cc, v);
-    amp[base + i] = sqrtf(v);
+  for (int g = 0; g < nc; g += AI_NT * AI_U) {
+    Raw8<IT> r[AI_U];
+#pragma unroll
+    for (int u = 0; u < AI_U; ++u) {
+      const int c = g + t + AI_NT * u;
+      if (c < nc) r[u].load(fr + 8 * static_cast<size_t>(c));
+    }
+#pragma unroll
+    for (int u = 0; u < AI_U; ++u) {
+      const int c = g + t + AI_NT * u;
+      if (c < nc) {
+        float d[8], v[8];
+        dark8(dark ? dark + 8 * static_cast<size_t>(c) : nullptr, d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          v[i] = clamp_sub(r[u].at(i), d[i]);
+          two_sum_add(s, cc, v[i]);
+          v[i] = sqrtf(v[i]);
+        }
+        float4 *o = reinterpret_cast<float4 *>(out + 8 * static_cast<size_t>(c));
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
   }
-  sh[threadIdx.x] = two_sum_value(s, cc);
+  sh[t] = two_sum_value(s, cc);
   __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  for (int w = AI_NT / 2; w > 0; w >>= 1) {
+    if (t < w) sh[t] += sh[t + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) isum[f0 + blockIdx.x] = sh[0];
+  if (t == 0) isum[f0 + blockIdx.x] = sh[0];
 }
 }  // namespace
 
@@ -519,13 +544,13 @@ cudaError_t launch_amp_ingest(const void *frames, int itype, const float *dark, 
   if (N == 512) return launch_amp_ingest_512(frames, itype, dark, amp, isum, f0, n, st);
   const int K = N * N;
   if (itype == EPIE_U16)
-    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp, isum,
+    amp_ingest_kernel<<<n, AI_NT, 0, st>>>(static_cast<const uint16_t *>(frames), dark, amp, isum,
                                           f0, K);
   else if (itype == EPIE_F16)
-    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const __half *>(frames), dark, amp, isum,
+    amp_ingest_kernel<<<n, AI_NT, 0, st>>>(static_cast<const __half *>(frames), dark, amp, isum,
                                           f0, K);
   else
-    amp_ingest_kernel<<<n, 1024, 0, st>>>(static_cast<const float *>(frames), dark, amp, isum, f0,
+    amp_ingest_kernel<<<n, AI_NT, 0, st>>>(static_cast<const float *>(frames), dark, amp, isum, f0,
                                           K);
   return cudaGetLastError();
 }

@@ -39,6 +39,7 @@
 #include <cmath>
 
 #include "epie_fused.cuh"
+#include "epie_ingest.cuh"
 
 namespace epie {
 
@@ -457,8 +458,9 @@ __global__ void __launch_bounds__(S_NT, 1) epie_fused128_kernel(GroupArgs a) {
 // kx = k1 + 16 (4 (m & 1) + i), k1 = 2 jj + (m >> 1), i = 0..3.
 // amp = sqrt(max(I - dark, 0)); isum = sum of max(I - dark, 0), two-sum in
 // FP32 per thread and a fixed-order FP64 sum over the block.  One block per
-// frame: the rows are read row by row (coalesced) into shared memory, then
-// written chunk by chunk (coalesced).
+// frame: each thread loads its chunks of the 128 rows (four 32-row tiles) as
+// 16-byte vectors, all in flight at once (TileLane), into shared memory; the
+// block then writes the frame chunk by chunk (coalesced).
 constexpr int AI_NT = 512, AI_PITCH = S_N + 1;  // odd pitch: conflict-free chunk reads
 constexpr size_t AI_SMEM = sizeof(float) * S_N * AI_PITCH + sizeof(double) * AI_NT;
 template <typename IT>
@@ -472,17 +474,14 @@ __global__ void __launch_bounds__(AI_NT) amp_ingest128_kernel(const IT *__restri
   const size_t fb = static_cast<size_t>(f0 + blockIdx.x) * S_N * S_N;
   const IT *fr = frames + fb;
   float4 *out = reinterpret_cast<float4 *>(amp + fb);
-  const int t = threadIdx.x, kx = t & (S_N - 1);
+  const int t = threadIdx.x;
   float s = 0.f, cc = 0.f;
-#pragma unroll 4
-  for (int pr = t >> 7; pr < S_N; pr += AI_NT / S_N) {
-    const int ky = freq_of_pos(pr);
-    float I = ival(fr[ky * S_N + kx]);
-    if (dark) I -= __ldg(dark + ky * S_N + kx);
-    I = fmaxf(I, 0.f);  // also maps NaN to 0
-    two_sum_add(s, cc, I);
-    rows[pr * AI_PITCH + kx] = sqrtf(I);
-  }
+  TileLane<S_N, AI_NT, IT> tl[S_N / 32];
+#pragma unroll
+  for (int q = 0; q < S_N / 32; ++q) tl[q].load(fr, freq_of_pos(32 * q + tl[q].yl));
+#pragma unroll
+  for (int q = 0; q < S_N / 32; ++q)
+    tl[q].store(rows + 32 * q * AI_PITCH, dark, freq_of_pos(32 * q + tl[q].yl), s, cc);
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < 4096 / AI_NT; ++u) {

@@ -50,6 +50,7 @@
 
 #include "epie_cluster.cuh"
 #include "epie_fft.cuh"
+#include "epie_ingest.cuh"
 #include "epie_internal.h"
 
 namespace epie {
@@ -538,9 +539,10 @@ __global__ void __launch_bounds__(S_NT, 1) epie_fused512_kernel(GroupArgs a) {
 // (wq * 8 + m) * 32 + yl, the values at kx = k1 + 32 (4 (m & 3) + i),
 // k1 = 2 wq + (m >> 2), i = 0..3.  amp = sqrt(max(I - dark, 0)); isum = sum
 // of max(I - dark, 0), two-sum in FP32 per thread and a fixed-order FP64 sum
-// over the block.  One block per frame walks the 16 tiles: the tile's 32
-// frequency rows are read row by row (coalesced) into shared memory, then
-// written chunk by chunk (coalesced).
+// over the block.  One block per frame walks the 16 tiles: each thread loads
+// its chunks of the tile's 32 frequency rows as 16-byte vectors (TileLane),
+// the next tile's loads are in flight while the current tile is written out
+// chunk by chunk (coalesced).
 constexpr int AI_NT = 512, AI_PITCH = S_N + 1;  // odd pitch: conflict-free chunk reads
 constexpr size_t AI_SMEM = sizeof(float) * 32 * AI_PITCH + sizeof(double) * AI_NT;
 template <typename IT>
@@ -556,17 +558,12 @@ __global__ void __launch_bounds__(AI_NT) amp_ingest512_kernel(const IT *__restri
   float4 *out = reinterpret_cast<float4 *>(amp + fb);
   const int t = threadIdx.x;
   float s = 0.f, cc = 0.f;
+  TileLane<S_N, AI_NT, IT> tl;
+  tl.load(fr, freq_of_pos(tl.yl));
   for (int q = 0; q < S_CL; ++q) {
-#pragma unroll 4
-    for (int yl = 0; yl < 32; ++yl) {
-      const int ky = freq_of_pos(32 * q + yl);
-      float I = ival(fr[ky * S_N + t]);
-      if (dark) I -= __ldg(dark + ky * S_N + t);
-      I = fmaxf(I, 0.f);  // also maps NaN to 0
-      two_sum_add(s, cc, I);
-      rows[yl * AI_PITCH + t] = sqrtf(I);
-    }
+    tl.store(rows, dark, freq_of_pos(32 * q + tl.yl), s, cc);
     __syncthreads();
+    if (q + 1 < S_CL) tl.load(fr, freq_of_pos(32 * (q + 1) + tl.yl));
 #pragma unroll
     for (int u = 0; u < 4096 / AI_NT; ++u) {
       const int cj = t + AI_NT * u, yl = cj & 31, wm = cj >> 5;
