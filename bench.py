@@ -35,6 +35,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ePIE frame-updates/s at 256^2 px (fused path), error vs FP64 oracle"
+
+
+def metric_name(N=256, path="fused"):
+    """The live workload's metric at frame side N on the given path (the
+    default frame side and path give METRIC)."""
+    return f"ePIE frame-updates/s at {N}^2 px ({path} path), error vs FP64 oracle"
+
 UNIT = "frame-updates/s"
 CHUNK = 500
 SM_COUNT = 152
@@ -295,7 +302,7 @@ def run_reference(args):
     value = per_step * args.steps / tot
     sample = (f"one coloured FP64 oracle sweep over the first {per_step} frames of the workload "
               "per step, single thread")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    line = {"impl": "reference", "metric": metric_name(args.frame_side, args.path), "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -453,7 +460,7 @@ def run_ours(args):
                 "timing_region": (f"{args.steps} further steps with events around each fused "
                                   f"launch ({timed_steps_ms:.2f} ms per step there)")}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    line = {"metric": metric_name(N, args.path), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "ms_per_step_median": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -48,3 +48,14 @@ def test_step_kernel_names_follow_frame_side_and_tile_shape():
     assert bench.step_kernel_name(128) == "epie_fused_kernel<128,4,...>"
     assert bench.step_kernel_name(128, 1) == "epie_fused128_kernel"
     assert bench.step_kernel_name(64) == "epie_fused_kernel<64,1,...>"
+
+
+def test_metric_names_the_frame_side_and_path():
+    assert bench.metric_name() == bench.METRIC
+    assert bench.metric_name(512) == "ePIE frame-updates/s at 512^2 px (fused path), error vs FP64 oracle"
+    assert "(plain path)" in bench.metric_name(256, "plain")
+
+
+def test_traffic_record_matches_the_committed_kernel():
+    # the record is retaken whenever the 256^2 step kernel's code changes
+    assert bench.measured_traffic() is not None

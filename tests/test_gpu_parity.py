@@ -541,3 +541,36 @@ def test_raw_intensity_staging(orc, N, ny, nx, step):
             outs.append((eng.object(), eng.probe(), e_g))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert abs(outs[0][2][0] - outs[1][2][0]) <= 1e-12 * outs[0][2][0]
+
+
+@pytest.mark.parametrize("N,shape,step", [(64, 0, 20), (128, 0, 65), (128, 1, 65), (256, 0, 130),
+                                          (512, 0, 300)])
+@pytest.mark.parametrize("dtype,code", [(np.uint16, B.EPIE_U16), (np.float16, B.EPIE_F16),
+                                        (np.float32, B.EPIE_F32)])
+def test_derived_amplitudes_equal_staged_rows(N, shape, step, dtype, code):
+    """The amplitudes derived at append (8 intensities per 16-byte load, in
+    each step kernel's tile layout) against the step kernel's own conversion
+    of the staged rows (EPIE_RAW_INTENSITY): object and probe bit-identical
+    after one sweep, for every intensity type and tile shape, with a dark
+    field above some intensities and, for the float types, negative and NaN
+    intensities (clamped to 0 on both paths).  The sweep error differs only
+    in the order of the intensity sum."""
+    d = synth.small_scan(N, 1, 3, step, seed=N + 31, dark=True, photons=1e7, dtype=dtype)
+    fr = d["frames"].copy()
+    if code != B.EPIE_U16:
+        fr[0, 3, 5] = np.nan
+        fr[1, N // 2, N // 3] = -4.0
+        fr[2, N - 1, 0] = np.nan
+        fr[2, 7, N - 2] = -0.0
+    st = textured_start(d)
+    outs = []
+    for flags in (0, B.EPIE_RAW_INTENSITY):
+        with engine(d, B.EPIE_COLOURED, st, ctas_per_frame=shape, intensity_dtype=code,
+                    flags=flags) as eng:
+            eng.set_dark(d["dark"])
+            eng.append(fr, d["pos"])
+            e_g = eng.iterate(1)
+            outs.append((eng.object(), eng.probe(), e_g))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.isfinite(outs[0][2][0])
+    assert abs(outs[0][2][0] - outs[1][2][0]) <= 1e-12 * outs[0][2][0]
