@@ -73,12 +73,13 @@ __global__ void dark_ingest_kernel(const float *__restrict__ src, float *__restr
 // row r sums members r, r + PR_ROWS, ... in order and the row sums are added
 // in row order, so the result does not depend on scheduling.  The partials
 // are read once, with the streaming hint, so their lines leave L2 before the
-// object's.
+// object's.  A thread issues the loads of 4 of its members at a time, the
+// last batch predicated past the last member.
 #ifndef EPIE_PROBE_ROWS
 #define EPIE_PROBE_ROWS 8
 #endif
 constexpr int PR_ROWS = EPIE_PROBE_ROWS, PR_THREADS = 32 * PR_ROWS;
-__global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
+__global__ void __launch_bounds__(PR_THREADS, 5) probe_reduce_kernel(
     float2 *__restrict__ P, const float2 *__restrict__ part, int n_members, int K, float scale,
     unsigned long long *pmax2_next, const int32_t *gstart, int group, int mean) {
   __shared__ float4 acc_sh[PR_ROWS][32];
@@ -98,18 +99,17 @@ __global__ void __launch_bounds__(PR_THREADS) probe_reduce_kernel(
   for (int base = blockIdx.x * 64; base < K; base += gridDim.x * 64) {
     const int i = base + 2 * tx;  // K is a multiple of 64
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int m = ty;
-    for (; m + 3 * PR_ROWS < n_members; m += 4 * PR_ROWS) {
-      const float4 a0 = ld(m, i), a1 = ld(m + PR_ROWS, i), a2 = ld(m + 2 * PR_ROWS, i),
-                   a3 = ld(m + 3 * PR_ROWS, i);
-      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
-      acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
-      acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
-      acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
-    }
-    for (; m < n_members; m += PR_ROWS) {
-      const float4 a0 = ld(m, i);
-      acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+    for (int m0 = ty; m0 < n_members; m0 += 4 * PR_ROWS) {
+      float4 a[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        a[k] = m0 + k * PR_ROWS < n_members ? ld(m0 + k * PR_ROWS, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (m0 + k * PR_ROWS < n_members) {  // members in order; none added past the last
+          acc.x += a[k].x; acc.y += a[k].y; acc.z += a[k].z; acc.w += a[k].w;
+        }
+      }
     }
     acc_sh[ty][tx] = acc;
     __syncthreads();
